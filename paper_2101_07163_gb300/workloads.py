@@ -1,0 +1,142 @@
+"""Seeded synthetic workloads: grids, parameters and initial moment fields.
+
+This module holds none of the lattice-Boltzmann arithmetic. It only states the physical
+parameters of the workloads (the paper's validation units W0 = tau0 = 1, dx = 0.4,
+dt = 0.008, Sec. 3.1.2-3.1.3) and builds the initial fields phi, U, rho, u that both the
+CUDA path and the test oracle turn into populations on their own.
+
+Initial crystal: a circular seed of radius R0 cells, phi = tanh((R0 - r) dx / (sqrt(2) W0)),
++1 in the ice and -1 in the vapour. Vapour: uniform supersaturation U0. Fluid: rho = 1 and,
+where the flow lattice is active, the inflow velocity weighted by the liquid fraction
+(1 - phi)/2 so that the ice starts at rest.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FREESLIP = 0, 1, 2, 3
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    steps: int
+    # physical parameters (W0/tau0 units; u_in and nu in lattice units)
+    dx: float = 0.4
+    dt: float = 0.008
+    W0: float = 1.0
+    tau0: float = 1.0
+    D: float = 2.0
+    lam: float = 0.0  # <= 0: beta = 0 choice lambda = tau0 D / (a2 W0^2)
+    L_sat: float = 1.0
+    eps: float = 0.05
+    kappa_N: float = 1.0
+    U0: float = 0.35
+    U_in: float = 0.0
+    u_in: float = 0.0
+    nu: float = 0.016
+    bc: tuple = (BC_PERIODIC,) * 4
+    flow: bool = False
+    # seed
+    cx: float = 0.0
+    cy: float = 0.0
+    R0: float = 6.0
+
+    def params(self) -> dict:
+        """Keyword arguments shared by the oracle and the CUDA binding."""
+        return dict(dx=self.dx, dt=self.dt, W0=self.W0, tau0=self.tau0, D=self.D,
+                    lam=self.lam, L_sat=self.L_sat, eps=self.eps, kappa_N=self.kappa_N,
+                    U_in=self.U_in, u_in=self.u_in, nu=self.nu, bc=tuple(self.bc),
+                    flow=self.flow)
+
+    def with_size(self, nx: int, ny: int, **kw) -> "Workload":
+        """The same physics on another grid, the seed kept at the same relative place."""
+        return dataclasses.replace(self, nx=nx, ny=ny, cx=self.cx * nx / self.nx,
+                                   cy=self.cy * ny / self.ny, **kw)
+
+    @property
+    def lattices(self) -> int:
+        return 3 if self.flow else 2
+
+    def inflow_vector(self) -> tuple[float, float]:
+        for face, (vx, vy) in enumerate([(1, 0), (-1, 0), (0, 1), (0, -1)]):
+            if self.bc[face] == BC_INLET:
+                return self.u_in * vx, self.u_in * vy
+        return 0.0, 0.0
+
+
+# 128 x 128 periodic, phase field + vapour only (flow at rest), seed R0 = 6 at the centre.
+C1 = Workload("hg_periodic_128x128", 128, 128, 2000, D=2.0, eps=0.05, U0=0.35,
+              cx=64, cy=64, R0=6.0)
+# 512 x 384 ventilated channel, all three lattices: inlet at -x (u = 0.02, U = 0.3),
+# zero-gradient outlet at +x, free-slip walls at -y/+y, seed R0 = 8 at (160, 192).
+C2 = Workload("ventilated_512x384", 512, 384, 20000, D=2.0, eps=0.05, U0=0.3, U_in=0.3,
+              u_in=0.02, nu=0.016, bc=(BC_INLET, BC_OUTLET, BC_FREESLIP, BC_FREESLIP),
+              flow=True, cx=160, cy=192, R0=8.0)
+# 2048 x 2048 periodic plate-regime snowflake, all three lattices, seed R0 = 10.
+C3 = Workload("plate_periodic_2048x2048", 2048, 2048, 50000, D=3.0, eps=0.05, U0=0.5,
+              flow=True, cx=1024, cy=1024, R0=10.0)
+
+WORKLOADS = {w.name: w for w in (C1, C2, C3)}
+
+
+def seed_fields(w: Workload) -> dict:
+    """Initial moments of a workload: circular seed, uniform U0, rho = 1, inflow velocity."""
+    y, x = np.mgrid[0:w.ny, 0:w.nx].astype(np.float64)
+    r = np.sqrt((x - w.cx) ** 2 + (y - w.cy) ** 2)
+    phi = np.tanh((w.R0 - r) * w.dx / (math.sqrt(2.0) * w.W0))
+    U = np.full_like(phi, w.U0)
+    rho = np.ones_like(phi)
+    vx, vy = w.inflow_vector()
+    liquid = 0.5 * (1.0 - phi)
+    return dict(phi=phi, U=U, rho=rho, ux=vx * liquid, uy=vy * liquid)
+
+
+def perturbed_fields(w: Workload, seed: int, amp_phi: float = 0.05, amp_U: float = 0.05,
+                     amp_rho: float = 0.01, amp_u: float = 0.01) -> dict:
+    """Seed fields plus seeded uniform noise (numpy PCG64), so every node is non-trivial."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    f = seed_fields(w)
+    shape = f["phi"].shape
+    f["phi"] = np.clip(f["phi"] + amp_phi * rng.uniform(-1, 1, shape), -1.0, 1.0)
+    f["U"] = f["U"] + amp_U * rng.uniform(-1, 1, shape)
+    f["rho"] = f["rho"] + amp_rho * rng.uniform(-1, 1, shape)
+    if w.flow:
+        f["ux"] = f["ux"] + amp_u * rng.uniform(-1, 1, shape)
+        f["uy"] = f["uy"] + amp_u * rng.uniform(-1, 1, shape)
+    return f
+
+
+def mirror_fields(w: Workload, seed: int, amp: float = 0.05) -> dict:
+    """Noise fields symmetric under x -> nx - x and y -> ny - y (mod n) about node (nx/2, ny/2).
+
+    Random values are drawn for one quadrant and reflected, so the field is exactly
+    mirror-symmetric. Velocities are odd under the mirror of their own axis.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nx, ny = w.nx, w.ny
+    assert nx % 2 == 0 and ny % 2 == 0
+
+    def sym(even_x=True, even_y=True):
+        a = rng.uniform(-1, 1, (ny, nx))
+        ix = (-np.arange(nx)) % nx
+        iy = (-np.arange(ny)) % ny
+        sx = 1.0 if even_x else -1.0
+        sy = 1.0 if even_y else -1.0
+        b = a + sx * a[:, ix]
+        b = b + sy * b[iy, :]
+        return 0.25 * b
+
+    c = dataclasses.replace(w, cx=nx // 2, cy=ny // 2)
+    f = seed_fields(c)
+    f["phi"] = np.clip(f["phi"] + amp * sym(), -1.0, 1.0)
+    f["U"] = f["U"] + amp * sym()
+    f["rho"] = f["rho"] + 0.2 * amp * sym()
+    f["ux"] = 0.2 * amp * sym(even_x=False)
+    f["uy"] = 0.2 * amp * sym(even_y=False)
+    return f
