@@ -1,0 +1,344 @@
+"""Benchmark of the fused coupled-lattice step on GB300.
+
+One bench step is one time step of the three coupled D2Q9 lattices (phase field, vapour,
+flow) over the whole grid of the plate-regime workload: 2048 x 2048 periodic, seed R0 = 10,
+U0 = 0.5, eps = 0.05, D = 3, FP32 state (956 MB, larger than the 129 MB L2, so no L2 flush
+is needed between steps). Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the test oracle, as it stands) on the host
+cores, on a band of the same workload per step. Under torchrun with N > 1 every rank runs
+an independent replica of the workload (no data-path collective) and rank 0 reports the
+aggregate over the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2101_07163_gb300 import workloads as W  # noqa: E402
+
+METRIC = "coupled-lattice MLUPS and % of HBM roofline at 1 GB300 vs FP64 CPU oracle error"
+ALGO_BYTES_PER_LUP = {3: 224, 2: 152}  # read + write of every population and of phi history
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=W.C3.name, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--nx", type=int, default=0, help="override grid (profiling runs)")
+    ap.add_argument("--ny", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(args) -> W.Workload:
+    w = W.WORKLOADS[args.workload]
+    if args.nx or args.ny:
+        w = w.with_size(args.nx or w.nx, args.ny or w.ny)
+    return w
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    backend = "nccl"
+    import torch
+    if not torch.cuda.is_available():
+        backend = "gloo"
+    else:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist.init_process_group(backend)
+    return dist, dist.get_rank(), dist.get_world_size()
+
+
+def max_over_ranks(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags)
+                          if f.lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_2101_07163_gb300/csrc/lbmice_step.cuh",
+                "paper_2101_07163_gb300/csrc/lbmice_device.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(nodes: int):
+    """DRAM bytes per launch from the committed ncu capture, if the kernel is unchanged."""
+    try:
+        with open(PROFILE_TRAFFIC) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None, None
+    if rec.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None, rec
+    return rec["dram_bytes_per_node"] * nodes, rec
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def oracle_run(w: W.Workload, fields: dict, seconds: float, min_steps: int = 2):
+    """Time the FP64 oracle on this workload, one full-grid step at a time."""
+    import oracle
+    o = oracle.Oracle(nx=w.nx, ny=w.ny, **w.params())
+    o.set_fields(**fields)
+    t0 = time.perf_counter()
+    n = 0
+    while n < min_steps or (time.perf_counter() - t0 < seconds and n < 64):
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return o, n, dt
+
+
+def run_reference(args):
+    dist, rank, world = dist_init()
+    if rank != 0:
+        return
+    import oracle
+    w = workload(args)
+    full = W.seed_fields(w)
+    # one bench step = one oracle step on a band of rows through the crystal, sized so that
+    # warmup + steps take about two minutes on one host core at ~3.5 MLUPS
+    total = max(1, args.steps + args.warmup)
+    rows = int(np.clip(round(120.0 * 3.5e6 / (w.nx * total)), 4, w.ny))
+    y0 = int(np.clip(int(w.cy) - rows // 2, 0, w.ny - rows))
+    band = W.Workload(**{**w.__dict__, "ny": rows, "cy": w.cy - y0})
+    fields = {k: np.ascontiguousarray(v[y0:y0 + rows]) for k, v in full.items()}
+    o = oracle.Oracle(nx=band.nx, ny=band.ny, **band.params())
+    o.set_fields(**fields)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = band.nx * band.ny * args.steps / dt / 1e6
+    sample = (f"{band.nx}x{band.ny} band (rows {y0}..{y0 + rows - 1}) of {w.name}, "
+              f"periodic, one FP64 oracle step per bench step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "grid": [w.nx, w.ny], "lattices": w.lattices,
+                   "sample_rows": rows},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import torch
+    dist, rank, world = dist_init()
+    from paper_2101_07163_gb300 import lbmice
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = workload(args)
+    nodes = w.nx * w.ny
+    stream = torch.cuda.Stream()
+    lat = lbmice.Lattice(w.nx, w.ny, stream=stream, **w.params())
+    lat.init_seed(w.cx, w.cy, w.R0, w.U0)
+    lat.step(args.warmup)
+    lat.sync()
+
+    # ---- device-timed region: K fused steps, state resident in HBM ----
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    dev_index = torch.cuda.current_device()
+    with ClockSampler(dev_index) as clk:
+        ev0.record(stream)
+        lat.step(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier(dist)
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(dist, ms)
+    stats = lat.stats()
+    finite = stats["nonfinite"] == 0
+
+    # ---- end-to-end through the C ABI with host buffers ----
+    f = W.seed_fields(w)
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in f.items()}
+    host = {k: t.numpy() for k, t in pinned.items()}
+    out_phi = torch.empty((w.ny, w.nx), dtype=torch.float32).pin_memory().numpy()
+    lat2 = lbmice.Lattice(w.nx, w.ny, stream=stream, **w.params())
+    lat2.set_fields(**host)  # warm the path once
+    lat2.step(min(args.warmup, 60))
+    lat2.sync()
+    barrier(dist)
+    t0 = time.perf_counter()
+    lat2.set_fields(**host)                       # H2D of the initial moments
+    lat2.step(args.steps)
+    st2 = lat2.stats()                            # D2H of the FP64 diagnostics
+    lat2.field(lbmice.PHI)                        # D2H of the result field
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(dist, e2e_s)
+    h2d = sum(v.nbytes for v in host.values())
+    d2h = out_phi.nbytes + 8 * lbmice.NSTATS
+    lat2.close()
+    del lat2
+
+    if rank != 0:
+        lat.close()
+        barrier(dist)
+        return
+
+    value = nodes * args.steps * world / (ms * 1e-3) / 1e6
+    per_launch_ms = ms / args.steps
+    algo = ALGO_BYTES_PER_LUP[w.lattices] * nodes
+    achieved = algo / (per_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    traffic, rec = profiled_traffic(nodes)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs copy bandwidth)"
+                if peak_kind == "measured" else peak_kind,
+                "algorithmic_bytes_per_lup": ALGO_BYTES_PER_LUP[w.lattices],
+                "kernel": "lbmice::step_kernel"}
+    if rec is not None:
+        roofline["traffic_source"] = rec.get("source")
+        if traffic is None:
+            roofline["traffic_note"] = "kernel changed since the ncu capture"
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "grid": [w.nx, w.ny], "lattices": w.lattices,
+                   "seed_R0": w.R0, "U0": w.U0, "eps": w.eps, "D": w.D,
+                   "state_bytes": int(nodes * (2 * 9 * w.lattices + 3) * 4),
+                   "l2_policy": "inputs larger than L2 (state > 129 MB), no flush",
+                   "parallelism": f"independent replicas x{world}"},
+        "roofline": roofline,
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "e2e": {"value": nodes * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "note": "set_fields from pinned host + K steps + stats + phi to host"},
+        "finite": bool(finite and st2["nonfinite"] == 0),
+    }
+
+    # ---- CPU baseline and error against the FP64 oracle, rank 0, N = 1 only ----
+    if world == 1 and not args.no_cpu_baseline:
+        fields = W.perturbed_fields(w, 2101, amp_phi=0.05, amp_u=0.01)
+        o, n, dt = oracle_run(w, fields, args.cpu_seconds)
+        lat.set_fields(**fields)
+        lat.step(n)
+        err = {"steps": n,
+               "max_dphi": float(np.abs(lat.field(lbmice.PHI) - o.field(0)).max()),
+               "max_dU": float(np.abs(lat.field(lbmice.U) - o.field(1)).max()),
+               "max_dux": float(np.abs(lat.field(lbmice.UX) - o.field(3)).max())}
+        line["cpu_baseline"] = {"value": nodes * n / dt / 1e6, "unit": "MLUPS", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{n} full-grid FP64 oracle steps of {w.name} "
+                                          f"(perturbed seed), single thread"}
+        line["oracle_error"] = err
+    print(json.dumps(line), flush=True)
+    lat.close()
+    barrier(dist)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

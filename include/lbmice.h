@@ -1,0 +1,174 @@
+/*
+ * lbmice.h -- C ABI of the GB300 (sm_103a) coupled lattice-Boltzmann ice-crystal step.
+ *
+ * Method: Tan, Hosseini, Seidel-Morgenstern, Thevenin, Lorenz, "Modeling ice crystal growth
+ * using the lattice Boltzmann method" (arXiv 2101.07163), Sec. 2.2. One call of
+ * lbmice_step(h, 1) advances, in one fused CUDA kernel, the three D2Q9 lattices of one grid:
+ *   - flow f (Sec. 2.2.1): BGK collision towards the second-order Hermite equilibrium at the
+ *     solid-damped velocity u* = (1 - phi)/2 u, plus the solid drag
+ *     F = -h eta_f (1 + phi)^2 (1 - phi) u / (4 W0^2), h = 2.757, by Guo forcing;
+ *   - vapour supersaturation g (Sec. 2.2.2): advection-diffusion BGK with
+ *     g^eq = w U (1 + c.u* / c_s^2), tau_g = D q(phi)/c_s^2 + 1/2, q = 1 - phi, and the
+ *     phase-change source -w (L_sat/2) d(phi)/dt;
+ *   - phase field h (Sec. 2.2.3, Eq. (d), Eq. (e)): the modified LB update with the a_s^2
+ *     time factor, source Q = phi - phi^3 + lambda U (1 - phi^2)^2, and anisotropy
+ *     a_s = 1 + eps cos(6 theta) from the E4 isotropic gradient of phi (Sec. 3.1.1,
+ *     Table 1).
+ * Unit conventions: W0, tau0, dx, dt and D share one unit system (the paper's validation
+ * units are W0 = tau0 = 1, dx = 0.4, dt = 0.008, Sec. 3.1.2); u_in and nu are in lattice
+ * units (dx/dt, dx^2/dt).
+ *
+ * Conventions of every entry point:
+ *   - Return LBMICE_OK (0) on success, a negative LBMICE_E* code on failure; no C++
+ *     exception crosses the ABI. lbmice_strerror() names a code.
+ *   - The handle owns all device memory it allocates; the caller owns every buffer it
+ *     passes in. Pointers marked "device" must be CUDA device pointers on the handle's
+ *     device; "host" pointers may be pageable or pinned.
+ *   - All GPU work is enqueued on the stream given to lbmice_create (0 = the legacy default
+ *     stream). Calls that return data to host memory synchronise that stream; the others
+ *     are asynchronous unless stated.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ *   - Fields are row-major float arrays of ny rows and nx columns (element (x, y) at
+ *     y * nx + x), unless stated otherwise.
+ *   - D2Q9 order of populations: c = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1)
+ *     (1,-1).
+ */
+#ifndef LBMICE_H_
+#define LBMICE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ----------------------------------------------------------------------- */
+#define LBMICE_OK 0
+#define LBMICE_EINVAL (-1)     /* bad argument: null pointer, size, range, buffer length */
+#define LBMICE_ECUDA (-2)      /* a CUDA runtime call or kernel launch failed */
+#define LBMICE_ENOMEM (-3)     /* device or pinned host allocation failed */
+#define LBMICE_ENONFINITE (-4) /* a NaN or Inf was found in phi, U or rho */
+#define LBMICE_EUNSTABLE (-5)  /* derived relaxation time <= 1/2 or inflow >= sound speed */
+#define LBMICE_ETIMEOUT (-6)   /* a bounded device-side wait gave up */
+
+/* ---- boundary kinds of the four faces (Sec. 3.1.3, Sec. 3.2.2) --------------------------
+ * PERIODIC: wrap (must be set on both faces of an axis).
+ * INLET:    ghost nodes hold vapour (phi = -1, a_s = 1) at U_in, with the flow equilibrium
+ *           at the adjacent node's density and velocity u_in along the inward normal.
+ * OUTLET:   zero-gradient: ghost nodes copy the adjacent node.
+ * FREESLIP: specular wall: ghost nodes are the mirror image of the adjacent node.        */
+#define LBMICE_BC_PERIODIC 0
+#define LBMICE_BC_INLET 1
+#define LBMICE_BC_OUTLET 2
+#define LBMICE_BC_FREESLIP 3
+
+/* ---- field selectors of lbmice_fields / lbmice_load ------------------------------------ */
+#define LBMICE_FIELD_PHI 0      /* phi = sum h (Sec. 2.2.3)                   float[ny][nx] */
+#define LBMICE_FIELD_U 1        /* U = sum g (Sec. 2.2.2)                     float[ny][nx] */
+#define LBMICE_FIELD_RHO 2      /* rho = sum f (Sec. 2.2.1); 1 without flow   float[ny][nx] */
+#define LBMICE_FIELD_UX 3       /* u*_x = (1-phi)/2 j_x/(rho + k/2)           float[ny][nx] */
+#define LBMICE_FIELD_UY 4       /* u*_y                                       float[ny][nx] */
+#define LBMICE_FIELD_PHI_PREV 5 /* phi one step earlier (d(phi)/dt history)   float[ny][nx] */
+#define LBMICE_FIELD_POPS 6     /* raw populations, planes h0..h8, g0..g8 and, with flow,
+                                   f0..f8: float[18 or 27][ny][nx]                        */
+
+#define LBMICE_NSTATS 6
+
+/* ---- parameters (Sec. 2.1, Sec. 2.2, Sec. 3) -------------------------------------------- */
+typedef struct lbmice_params {
+  int32_t nx, ny;       /* grid nodes, each >= 4                                           */
+  double dx, dt;        /* grid and time step (default 0.4, 0.008)                         */
+  double W0, tau0;      /* interface width and time (default 1, 1)                         */
+  double D;             /* vapour diffusivity (default 2)                                  */
+  double lambda;        /* coupling; <= 0 selects tau0 D / (a2 W0^2), a2 = 0.6267 (beta = 0)*/
+  double L_sat;         /* vapour absorption rate at the interface (default 1)             */
+  double eps;           /* six-fold anisotropy strength eps_xy, 0 <= eps < 1 (default 0.05)*/
+  double kappa_N;       /* factor of the anisotropic flux: 1 = a_s da_s/d(grad phi)
+                           (default), 2 = the printed d(a_s^2)/d(grad phi)                 */
+  double U_in;          /* supersaturation carried in by an INLET face                     */
+  double u_in;          /* inflow speed, lattice units, along the inlet's inward normal    */
+  double nu;            /* kinematic viscosity, lattice units (default 0.016)              */
+  int32_t bc[4];        /* faces -x, +x, -y, +y: LBMICE_BC_*                               */
+  int32_t flow;         /* 1: evolve the flow lattice f; 0: fluid at rest, f not stored    */
+  int32_t check_every;  /* lbmice_step checks for NaN/Inf every this many steps (0: never) */
+} lbmice_params;
+
+typedef struct lbmice_ctx lbmice_t;
+
+/* Fill *p with the defaults above for an nx x ny periodic grid without flow.
+ * Returns LBMICE_EINVAL if p is null. */
+int lbmice_params_default(lbmice_params* p, int32_t nx, int32_t ny);
+
+/* Validate *p, derive the lattice constants (Sec. 2.1 beta = 0 lambda, Sec. 2.2.1
+ * tau_f = nu/c_s^2 + 1/2), allocate the state on the current CUDA device and return a
+ * handle in *out. stream: a cudaStream_t (0 = legacy default stream); all work of the
+ * handle runs on it. Errors: EINVAL (null, size, face kinds, unpaired PERIODIC, eps range),
+ * EUNSTABLE (tau_f <= 1/2 with flow, |u_in| >= 1/sqrt(3)), ENOMEM, ECUDA. On error *out is
+ * set to NULL and nothing is leaked. The state is zero until an init call. */
+int lbmice_create(const lbmice_params* p, void* stream, lbmice_t** out);
+
+/* Initial condition of Sec. 3.1.2 / Sec. 3.2: circular seed of radius R0 cells centred at
+ * (cx, cy) (node coordinates), phi = tanh((R0 - r) dx / (sqrt(2) W0)), uniform U = U0,
+ * rho = 1, velocity u_in along the inlet normal times the liquid fraction (1 - phi)/2
+ * (zero without an inlet). Populations are set to the equilibria of these moments and the
+ * phi history to phi. Asynchronous. Errors: EINVAL, ECUDA. */
+int lbmice_init_seed(lbmice_t* h, double cx, double cy, double R0, double U0);
+
+/* Initial condition from moment fields: double arrays [ny][nx] (host or device, per
+ * on_device). phi and U are required; rho (default 1), ux, uy (default 0) may be NULL and
+ * are ignored when params.flow = 0 (the fluid is at rest).
+ * Populations become the equilibria of (phi, U, rho, u) -- h^eq of Eq. (e) with the
+ * anisotropic flux of phi's E4 gradient, g^eq of Sec. 2.2.2, f^eq of Sec. 2.2.1 -- and the
+ * phi history is set to sum h. Host arrays are copied before the call returns (the stream
+ * is synchronised); device arrays are read asynchronously. Errors: EINVAL, ENOMEM, ECUDA. */
+int lbmice_set_fields(lbmice_t* h, const double* phi, const double* U, const double* rho,
+                      const double* ux, const double* uy, int32_t on_device);
+
+/* Advance nsteps >= 0 time steps (one fused kernel per step; chunks of steps are replayed
+ * as CUDA graphs). Asynchronous unless params.check_every > 0, in which case the stream is
+ * synchronised every check_every steps and LBMICE_ENONFINITE is returned as soon as a NaN or
+ * Inf appears in phi, U or rho. Errors: EINVAL, ECUDA, ENONFINITE. */
+int lbmice_step(lbmice_t* h, int64_t nsteps);
+
+/* Copy one field (LBMICE_FIELD_*) of the current state into dst, which holds bytes bytes
+ * (must be at least the field's size: 4 nx ny, or 4 nx ny times 18 or 27 for POPS).
+ * dst_on_device: 1 = device pointer (asynchronous), 0 = host pointer (the call
+ * synchronises the stream before returning). Errors: EINVAL, ECUDA. */
+int lbmice_fields(lbmice_t* h, int32_t which, void* dst, size_t bytes, int32_t dst_on_device);
+
+/* Overwrite the state from a checkpoint: which = LBMICE_FIELD_POPS (layout as in
+ * lbmice_fields; phi is recomputed as sum h) or LBMICE_FIELD_PHI_PREV. src holds bytes
+ * bytes, on the device (1) or host (0). Loading both restores a state exactly.
+ * Errors: EINVAL, ECUDA. */
+int lbmice_load(lbmice_t* h, int32_t which, const void* src, size_t bytes,
+                int32_t src_on_device);
+
+/* FP64 reductions of the current state into out[LBMICE_NSTATS] (host):
+ *   out[0] solid area   sum (1 + phi)/2 dx^2
+ *   out[1] flow mass    sum rho                 (exactly conserved without inlet/outlet)
+ *   out[2] vapour invariant sum U + (L_sat/2) sum phi_prev (exact with periodic faces)
+ *   out[3] sum phi
+ *   out[4] number of nodes where phi, U or rho is NaN or Inf
+ *   out[5] time steps taken since the last init
+ * Synchronises the stream. Errors: EINVAL, ECUDA. */
+int lbmice_stats(lbmice_t* h, double out[LBMICE_NSTATS]);
+
+/* Wait for the handle's stream and report any pending asynchronous CUDA error. */
+int lbmice_sync(lbmice_t* h);
+
+/* Number of time steps taken since the last init (host counter, no synchronisation). */
+int64_t lbmice_steps_done(const lbmice_t* h);
+
+/* Release the handle and all device memory it owns (synchronises the stream first).
+ * Null is accepted. */
+int lbmice_destroy(lbmice_t* h);
+
+/* Static description of an error code. */
+const char* lbmice_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMICE_H_ */

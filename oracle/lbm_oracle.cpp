@@ -486,9 +486,11 @@ void init_fields(Oracle<T>* o, const double* phi0, const double* U0, const doubl
       T gx, gy, as, Nx, Ny;
       gradient_at(*o, phi, x, y, &gx, &gy);
       anisotropy(gx, gy, o->p.eps, o->p.kappa_N, &as, &Nx, &Ny);
-      const T rho = rho0 ? T(rho0[i]) : T(1.0);
-      const T ux = ux0 ? T(ux0[i]) : T(0.0);
-      const T uy = uy0 ? T(uy0[i]) : T(0.0);
+      // without the flow lattice the fluid is at rest (rho = 1, u = 0)
+      const bool fl = o->p.flow != 0;
+      const T rho = (fl && rho0) ? T(rho0[i]) : T(1.0);
+      const T ux = (fl && ux0) ? T(ux0[i]) : T(0.0);
+      const T uy = (fl && uy0) ? T(uy0[i]) : T(0.0);
       for (int a = 0; a < 9; ++a) {
         o->h[a][i] = heq(a, phi[i], Nx, Ny, o->d.Dphi);
         o->g[a][i] = geq(a, T(U0[i]), ux, uy);

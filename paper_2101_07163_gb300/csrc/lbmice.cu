@@ -1,0 +1,424 @@
+// C ABI of the coupled lattice-Boltzmann ice-crystal step (include/lbmice.h): parameter
+// derivation, device state, kernel launches and CUDA-graph replay of step chunks.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbmice.h"
+#include "lbmice_aux.cuh"
+#include "lbmice_step.cuh"
+
+using namespace lbmice;
+
+namespace {
+
+constexpr double kA2 = 0.6267;   // Sec. 2.1: a2 of the sharp-interface mapping
+constexpr double kHdrag = 2.757; // Sec. 2.2.1: drag constant h
+constexpr int kTX = 32, kTY = 8; // destination tile of the step kernel
+// Steps per captured graph: a multiple of 6, so the population double buffer (period 2) and
+// the phi triple buffer (period 3) are back in their slots after each replay.
+constexpr int kGraphSteps = 60;
+constexpr int kStatBlocks = 608; // 4 x 152 SMs
+
+}  // namespace
+
+struct lbmice_ctx {
+  lbmice_params p;
+  Consts C;
+  double Dphi3, lambda;
+  int device = 0;
+  cudaStream_t stream = nullptr;   // caller's stream: every launch goes here
+  cudaStream_t capture = nullptr;  // private stream used only to record graphs
+  int nplanes = 0;
+  float* pops[2] = {nullptr, nullptr};
+  float* phi[3] = {nullptr, nullptr, nullptr};
+  float* fieldbuf = nullptr;       // one contiguous float field, for host exports
+  double* stat_partial = nullptr;
+  double* stat_out = nullptr;
+  double* stat_host = nullptr;     // pinned
+  cudaGraphExec_t graph = nullptr;
+  int64_t step = 0;
+};
+
+namespace {
+
+inline dim3 node_grid(const Consts& C, dim3 blk) {
+  return dim3((C.nx + blk.x - 1) / blk.x, (C.ny + blk.y - 1) / blk.y);
+}
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return LBMICE_OK;
+  return e == cudaErrorMemoryAllocation ? LBMICE_ENOMEM : LBMICE_ECUDA;
+}
+
+#define LB_TRY(expr)                          \
+  do {                                        \
+    int rc_ = cuda_err(expr);                 \
+    if (rc_ != LBMICE_OK) return rc_;         \
+  } while (0)
+
+int validate(const lbmice_params& p) {
+  if (p.nx < 4 || p.ny < 4) return LBMICE_EINVAL;
+  const long long pitch = ((long long)p.nx + 31) / 32 * 32;
+  if (pitch * p.ny >= (1LL << 31)) return LBMICE_EINVAL;
+  if (!(p.dx > 0) || !(p.dt > 0) || !(p.W0 > 0) || !(p.tau0 > 0)) return LBMICE_EINVAL;
+  if (!(p.D >= 0) || !(p.eps >= 0 && p.eps < 1) || !(p.kappa_N >= 0)) return LBMICE_EINVAL;
+  if (!std::isfinite(p.L_sat) || !std::isfinite(p.U_in) || !std::isfinite(p.lambda))
+    return LBMICE_EINVAL;
+  for (int f = 0; f < 4; ++f)
+    if (p.bc[f] < LBMICE_BC_PERIODIC || p.bc[f] > LBMICE_BC_FREESLIP) return LBMICE_EINVAL;
+  if ((p.bc[0] == LBMICE_BC_PERIODIC) != (p.bc[1] == LBMICE_BC_PERIODIC)) return LBMICE_EINVAL;
+  if ((p.bc[2] == LBMICE_BC_PERIODIC) != (p.bc[3] == LBMICE_BC_PERIODIC)) return LBMICE_EINVAL;
+  if (p.flow != 0 && p.flow != 1) return LBMICE_EINVAL;
+  if (p.check_every < 0) return LBMICE_EINVAL;
+  if (!std::isfinite(p.u_in) || std::fabs(p.u_in) >= std::sqrt(1.0 / 3.0)) return LBMICE_EUNSTABLE;
+  if (p.flow && !(p.nu > 0)) return LBMICE_EUNSTABLE;  // tau_f = 3 nu + 1/2 must exceed 1/2
+  return LBMICE_OK;
+}
+
+void derive(lbmice_t* h) {
+  const lbmice_params& p = h->p;
+  Consts& C = h->C;
+  std::memset(&C, 0, sizeof(C));
+  C.nx = p.nx;
+  C.ny = p.ny;
+  C.pitch = (p.nx + 31) / 32 * 32;
+  C.plane = (long long)C.pitch * p.ny;
+  for (int f = 0; f < 4; ++f) C.bc[f] = p.bc[f];
+  const double Dphi = (p.W0 * p.W0 / p.tau0) * p.dt / (p.dx * p.dx);
+  h->Dphi3 = 3.0 * Dphi;
+  h->lambda = p.lambda > 0 ? p.lambda : p.tau0 * p.D / (kA2 * p.W0 * p.W0);
+  const double Wlat = p.W0 / p.dx;
+  const double tau_f = p.nu * 3.0 + 0.5;
+  C.Dphi3 = (float)h->Dphi3;
+  C.dt_tau0 = (float)(p.dt / p.tau0);
+  C.lambda = (float)h->lambda;
+  C.Dlat3 = (float)(3.0 * p.D * p.dt / (p.dx * p.dx));
+  C.half_Lsat = (float)(0.5 * p.L_sat);
+  C.eps = (float)p.eps;
+  C.kN6eps = (float)(p.kappa_N * 6.0 * p.eps);
+  C.kdrag = (float)(kHdrag * p.nu / (4.0 * Wlat * Wlat));
+  C.inv_tau_f = (float)(1.0 / tau_f);
+  C.guo = (float)(1.0 - 0.5 / tau_f);
+  C.U_in = (float)p.U_in;
+  const double nxs[4] = {1, -1, 0, 0}, nys[4] = {0, 0, 1, -1};
+  for (int f = 0; f < 4; ++f) {
+    C.uin_x[f] = (float)(p.u_in * nxs[f]);
+    C.uin_y[f] = (float)(p.u_in * nys[f]);
+  }
+}
+
+void release(lbmice_t* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (float* b : h->pops) if (b) cudaFree(b);
+  for (float* b : h->phi) if (b) cudaFree(b);
+  if (h->fieldbuf) cudaFree(h->fieldbuf);
+  if (h->stat_partial) cudaFree(h->stat_partial);
+  if (h->stat_out) cudaFree(h->stat_out);
+  if (h->stat_host) cudaFreeHost(h->stat_host);
+  if (h->capture) cudaStreamDestroy(h->capture);
+  delete h;
+}
+
+size_t pop_bytes(const lbmice_t* h) { return sizeof(float) * h->nplanes * (size_t)h->C.plane; }
+
+int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
+  StepPtrs P;
+  P.pin = h->pops[s & 1];
+  P.pout = h->pops[(s + 1) & 1];
+  P.phi_n = h->phi[s % 3];
+  P.phi_nm1 = h->phi[(s + 2) % 3];
+  P.phi_np1 = h->phi[(s + 1) % 3];
+  const dim3 blk(kTX, kTY);
+  const dim3 grd = node_grid(h->C, blk);
+  if (h->p.flow)
+    step_kernel<kTX, kTY, true>
+        <<<grd, blk, Tile<kTX, kTY>::smem_bytes<true>(), st>>>(h->C, P);
+  else
+    step_kernel<kTX, kTY, false>
+        <<<grd, blk, Tile<kTX, kTY>::smem_bytes<false>(), st>>>(h->C, P);
+  return cuda_err(cudaGetLastError());
+}
+
+int ensure_graph(lbmice_t* h) {
+  if (h->graph) return LBMICE_OK;
+  cudaGraph_t g = nullptr;
+  LB_TRY(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
+  int rc = LBMICE_OK;
+  for (int s = 0; s < kGraphSteps && rc == LBMICE_OK; ++s) rc = launch_step(h, s, h->capture);
+  cudaError_t e = cudaStreamEndCapture(h->capture, &g);
+  if (rc != LBMICE_OK) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e != cudaSuccess) return cuda_err(e);
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { h->graph = nullptr; return cuda_err(e); }
+  return LBMICE_OK;
+}
+
+int run_stats(lbmice_t* h) {
+  const int64_t s = h->step;
+  stats_partial_kernel<<<kStatBlocks, kStatThreads, 0, h->stream>>>(
+      h->C, h->p.flow, 0.5 * h->p.dx * h->p.dx, 0.5 * h->p.L_sat, h->pops[s & 1],
+      h->phi[s % 3], h->phi[(s + 2) % 3], h->stat_partial);
+  LB_TRY(cudaGetLastError());
+  stats_final_kernel<<<1, 32, 0, h->stream>>>(h->stat_partial, kStatBlocks, h->stat_out);
+  LB_TRY(cudaGetLastError());
+  LB_TRY(cudaMemcpyAsync(h->stat_host, h->stat_out, kNStat * sizeof(double),
+                         cudaMemcpyDeviceToHost, h->stream));
+  LB_TRY(cudaStreamSynchronize(h->stream));
+  return LBMICE_OK;
+}
+
+int equilibrium_from(lbmice_t* h, const double* phi, const double* U, const double* rho,
+                     const double* ux, const double* uy) {
+  if (!h->p.flow) ux = uy = rho = nullptr;  // fluid at rest: g^eq sees u = 0
+  const dim3 blk(32, 8);
+  const dim3 grd = node_grid(h->C, blk);
+  const double eps = h->p.eps, kN6eps = h->p.kappa_N * 6.0 * h->p.eps;
+  if (h->p.flow)
+    equilibrium_kernel<true><<<grd, blk, 0, h->stream>>>(h->C, h->Dphi3, eps, kN6eps, phi, U,
+                                                         rho, ux, uy, h->pops[0], h->phi[0],
+                                                         h->phi[2]);
+  else
+    equilibrium_kernel<false><<<grd, blk, 0, h->stream>>>(h->C, h->Dphi3, eps, kN6eps, phi,
+                                                          U, rho, ux, uy, h->pops[0],
+                                                          h->phi[0], h->phi[2]);
+  LB_TRY(cudaGetLastError());
+  h->step = 0;
+  return LBMICE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbmice_params_default(lbmice_params* p, int32_t nx, int32_t ny) {
+  if (!p) return LBMICE_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->nx = nx;
+  p->ny = ny;
+  p->dx = 0.4;
+  p->dt = 0.008;
+  p->W0 = 1.0;
+  p->tau0 = 1.0;
+  p->D = 2.0;
+  p->lambda = 0.0;
+  p->L_sat = 1.0;
+  p->eps = 0.05;
+  p->kappa_N = 1.0;
+  p->nu = 0.016;
+  for (int f = 0; f < 4; ++f) p->bc[f] = LBMICE_BC_PERIODIC;
+  return LBMICE_OK;
+}
+
+int lbmice_create(const lbmice_params* p, void* stream, lbmice_t** out) {
+  if (!out) return LBMICE_EINVAL;
+  *out = nullptr;
+  if (!p) return LBMICE_EINVAL;
+  int rc = validate(*p);
+  if (rc != LBMICE_OK) return rc;
+  lbmice_t* h = new (std::nothrow) lbmice_ctx();
+  if (!h) return LBMICE_ENOMEM;
+  h->p = *p;
+  derive(h);
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->nplanes = p->flow ? 27 : 18;
+  cudaError_t e = cudaGetDevice(&h->device);
+  const size_t field_bytes = sizeof(float) * (size_t)p->nx * p->ny;
+  const size_t phi_bytes = sizeof(float) * (size_t)h->C.plane;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&h->pops[i], pop_bytes(h));
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&h->phi[i], phi_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->fieldbuf, field_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->stat_partial, sizeof(double) * kStatBlocks * kNStat);
+  if (e == cudaSuccess) e = cudaMalloc(&h->stat_out, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->stat_host, sizeof(double) * 8);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    e = cudaMemsetAsync(h->pops[i], 0, pop_bytes(h), h->stream);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    e = cudaMemsetAsync(h->phi[i], 0, phi_bytes, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    release(h);
+    cudaGetLastError();  // clear a sticky-free error state left by a failed allocation
+    return cuda_err(e);
+  }
+  *out = h;
+  return LBMICE_OK;
+}
+
+int lbmice_init_seed(lbmice_t* h, double cx, double cy, double R0, double U0) {
+  if (!h || !std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(R0) ||
+      !std::isfinite(U0))
+    return LBMICE_EINVAL;
+  // The second population buffer is free before the first step: it holds the five double
+  // seed fields (40 bytes per node; it has 72 or 108).
+  const size_t n = (size_t)h->p.nx * h->p.ny;
+  double* f = reinterpret_cast<double*>(h->pops[1]);
+  // velocity of the first inlet face along its inward normal (the fluid rests otherwise)
+  double ux = 0.0, uy = 0.0;
+  const double nxs[4] = {1, -1, 0, 0}, nys[4] = {0, 0, 1, -1};
+  for (int face = 0; face < 4; ++face)
+    if (h->p.flow && h->p.bc[face] == LBMICE_BC_INLET) {
+      ux = h->p.u_in * nxs[face];
+      uy = h->p.u_in * nys[face];
+      break;
+    }
+  const dim3 blk(32, 8);
+  const dim3 grd = node_grid(h->C, blk);
+  seed_kernel<<<grd, blk, 0, h->stream>>>(h->p.nx, h->p.ny, cx, cy, R0, U0,
+                                          std::sqrt(2.0) * h->p.W0 / h->p.dx, ux, uy, f,
+                                          f + n, f + 2 * n, f + 3 * n, f + 4 * n);
+  LB_TRY(cudaGetLastError());
+  return equilibrium_from(h, f, f + n, f + 2 * n, f + 3 * n, f + 4 * n);
+}
+
+int lbmice_set_fields(lbmice_t* h, const double* phi, const double* U, const double* rho,
+                      const double* ux, const double* uy, int32_t on_device) {
+  if (!h || !phi || !U || (on_device != 0 && on_device != 1)) return LBMICE_EINVAL;
+  if (on_device) return equilibrium_from(h, phi, U, rho, ux, uy);
+  const size_t n = (size_t)h->p.nx * h->p.ny;
+  double* f = reinterpret_cast<double*>(h->pops[1]);
+  const double* src[5] = {phi, U, rho, ux, uy};
+  const double* dev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  for (int k = 0; k < 5; ++k) {
+    if (!src[k]) continue;
+    LB_TRY(cudaMemcpyAsync(f + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice,
+                           h->stream));
+    dev[k] = f + k * n;
+  }
+  int rc = equilibrium_from(h, dev[0], dev[1], dev[2], dev[3], dev[4]);
+  if (rc != LBMICE_OK) return rc;
+  // pageable sources may be reused by the caller once this returns
+  LB_TRY(cudaStreamSynchronize(h->stream));
+  return LBMICE_OK;
+}
+
+int lbmice_step(lbmice_t* h, int64_t nsteps) {
+  if (!h || nsteps < 0) return LBMICE_EINVAL;
+  int64_t left = nsteps;
+  const int64_t every = h->p.check_every;
+  while (left > 0) {
+    int64_t chunk = left;
+    if (every > 0) chunk = std::min<int64_t>(left, every - (h->step % every));
+    int64_t done = 0;
+    while (done < chunk) {
+      if (h->step % 6 == 0 && chunk - done >= kGraphSteps) {
+        int rc = ensure_graph(h);
+        if (rc != LBMICE_OK) return rc;
+        LB_TRY(cudaGraphLaunch(h->graph, h->stream));
+        h->step += kGraphSteps;
+        done += kGraphSteps;
+      } else {
+        int rc = launch_step(h, h->step, h->stream);
+        if (rc != LBMICE_OK) return rc;
+        h->step += 1;
+        done += 1;
+      }
+    }
+    left -= chunk;
+    if (every > 0 && h->step % every == 0) {
+      int rc = run_stats(h);
+      if (rc != LBMICE_OK) return rc;
+      if (h->stat_host[4] != 0.0) return LBMICE_ENONFINITE;
+    }
+  }
+  return LBMICE_OK;
+}
+
+int lbmice_fields(lbmice_t* h, int32_t which, void* dst, size_t bytes, int32_t dst_on_device) {
+  if (!h || !dst || which < 0 || which > LBMICE_FIELD_POPS ||
+      (dst_on_device != 0 && dst_on_device != 1))
+    return LBMICE_EINVAL;
+  const int64_t s = h->step;
+  const size_t nx = h->p.nx, ny = h->p.ny;
+  if (which == LBMICE_FIELD_POPS) {
+    const size_t need = sizeof(float) * h->nplanes * nx * ny;
+    if (bytes < need) return LBMICE_EINVAL;
+    LB_TRY(cudaMemcpy2DAsync(dst, nx * sizeof(float), h->pops[s & 1],
+                             h->C.pitch * sizeof(float), nx * sizeof(float),
+                             (size_t)h->nplanes * ny,
+                             dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             h->stream));
+  } else {
+    const size_t need = sizeof(float) * nx * ny;
+    if (bytes < need) return LBMICE_EINVAL;
+    float* out = dst_on_device ? static_cast<float*>(dst) : h->fieldbuf;
+    const dim3 blk(32, 8);
+    moment_kernel<<<node_grid(h->C, blk), blk, 0, h->stream>>>(
+        h->C, which, h->p.flow, h->pops[s & 1], h->phi[s % 3], h->phi[(s + 2) % 3], out);
+    LB_TRY(cudaGetLastError());
+    if (!dst_on_device)
+      LB_TRY(cudaMemcpyAsync(dst, h->fieldbuf, need, cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (!dst_on_device) LB_TRY(cudaStreamSynchronize(h->stream));
+  return LBMICE_OK;
+}
+
+int lbmice_load(lbmice_t* h, int32_t which, const void* src, size_t bytes,
+                int32_t src_on_device) {
+  if (!h || !src || (src_on_device != 0 && src_on_device != 1)) return LBMICE_EINVAL;
+  if (which != LBMICE_FIELD_POPS && which != LBMICE_FIELD_PHI_PREV) return LBMICE_EINVAL;
+  const int64_t s = h->step;
+  const size_t nx = h->p.nx, ny = h->p.ny;
+  const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (which == LBMICE_FIELD_POPS) {
+    if (bytes < sizeof(float) * h->nplanes * nx * ny) return LBMICE_EINVAL;
+    LB_TRY(cudaMemcpy2DAsync(h->pops[s & 1], h->C.pitch * sizeof(float), src,
+                             nx * sizeof(float), nx * sizeof(float), (size_t)h->nplanes * ny,
+                             kind, h->stream));
+    const dim3 blk(32, 8);
+    phi_from_pops_kernel<<<node_grid(h->C, blk), blk, 0, h->stream>>>(h->C, h->pops[s & 1],
+                                                                      h->phi[s % 3]);
+    LB_TRY(cudaGetLastError());
+  } else {
+    if (bytes < sizeof(float) * nx * ny) return LBMICE_EINVAL;
+    LB_TRY(cudaMemcpy2DAsync(h->phi[(s + 2) % 3], h->C.pitch * sizeof(float), src,
+                             nx * sizeof(float), nx * sizeof(float), ny, kind, h->stream));
+  }
+  if (!src_on_device) LB_TRY(cudaStreamSynchronize(h->stream));
+  return LBMICE_OK;
+}
+
+int lbmice_stats(lbmice_t* h, double out[LBMICE_NSTATS]) {
+  if (!h || !out) return LBMICE_EINVAL;
+  int rc = run_stats(h);
+  if (rc != LBMICE_OK) return rc;
+  for (int k = 0; k < kNStat; ++k) out[k] = h->stat_host[k];
+  out[5] = (double)h->step;
+  return LBMICE_OK;
+}
+
+int lbmice_sync(lbmice_t* h) {
+  if (!h) return LBMICE_EINVAL;
+  LB_TRY(cudaStreamSynchronize(h->stream));
+  LB_TRY(cudaGetLastError());
+  return LBMICE_OK;
+}
+
+int64_t lbmice_steps_done(const lbmice_t* h) { return h ? h->step : -1; }
+
+int lbmice_destroy(lbmice_t* h) {
+  if (!h) return LBMICE_OK;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  release(h);
+  return cuda_err(e);
+}
+
+const char* lbmice_strerror(int code) {
+  switch (code) {
+    case LBMICE_OK: return "ok";
+    case LBMICE_EINVAL: return "invalid argument";
+    case LBMICE_ECUDA: return "CUDA error";
+    case LBMICE_ENOMEM: return "out of memory";
+    case LBMICE_ENONFINITE: return "non-finite value in phi, U or rho";
+    case LBMICE_EUNSTABLE: return "unstable parameters (relaxation time or inflow speed)";
+    case LBMICE_ETIMEOUT: return "device-side wait timed out";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// Auxiliary kernels: equilibrium initialisation from moment fields, the circular seed, moment
+// export, checkpoint support and the FP64 diagnostic reductions.
+#pragma once
+
+#include "lbmice_device.cuh"
+
+namespace lbmice {
+
+// Circular seed (Sec. 3.1.2): phi = tanh((R0 - r) dx / (sqrt(2) W0)), U = U0, rho = 1,
+// velocity = inlet velocity times the liquid fraction (1 - phi)/2. Fields are contiguous
+// [ny][nx] doubles.
+__global__ void seed_kernel(int nx, int ny, double cx, double cy, double R0, double U0,
+                            double width, double ux_in, double uy_in, double* phi, double* U,
+                            double* rho, double* ux, double* uy) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= nx || Y >= ny) return;
+  const long long i = (long long)Y * nx + X;
+  const double dx = X - cx, dy = Y - cy;
+  const double p = tanh((R0 - sqrt(dx * dx + dy * dy)) / width);
+  phi[i] = p;
+  U[i] = U0;
+  rho[i] = 1.0;
+  const double liquid = 0.5 * (1.0 - p);
+  ux[i] = ux_in * liquid;
+  uy[i] = uy_in * liquid;
+}
+
+// Populations at the equilibria of given moments, computed in double and stored as float:
+// h^eq (Eq. (e)) with the anisotropic flux of the E4 gradient of phi, g^eq (Sec. 2.2.2),
+// f^eq (Sec. 2.2.1). The stored phi and its history both become sum h.
+template <bool FLOW>
+__global__ void equilibrium_kernel(const Consts C, double Dphi3, double eps, double kN6eps,
+                                   const double* __restrict__ phi0,
+                                   const double* __restrict__ U0,
+                                   const double* __restrict__ rho0,
+                                   const double* __restrict__ ux0,
+                                   const double* __restrict__ uy0, float* __restrict__ pops,
+                                   float* __restrict__ phi_cur, float* __restrict__ phi_prev) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= C.nx || Y >= C.ny) return;
+  auto P = [&](int x, int y) -> double {
+    int gx, gy;
+    if (axis_phi(x, C.nx, C.bc[0], C.bc[1], gx) && axis_phi(y, C.ny, C.bc[2], C.bc[3], gy))
+      return phi0[(long long)gy * C.nx + gx];
+    return -1.0;
+  };
+  const long long i = (long long)Y * C.nx + X;
+  const double ph = phi0[i];
+  const double gx = (1.0 / 3.0) * (P(X + 1, Y) - P(X - 1, Y)) +
+                    (1.0 / 12.0) * ((P(X + 1, Y + 1) - P(X - 1, Y + 1)) +
+                                    (P(X + 1, Y - 1) - P(X - 1, Y - 1)));
+  const double gy = (1.0 / 3.0) * (P(X, Y + 1) - P(X, Y - 1)) +
+                    (1.0 / 12.0) * ((P(X + 1, Y + 1) - P(X + 1, Y - 1)) +
+                                    (P(X - 1, Y + 1) - P(X - 1, Y - 1)));
+  double as, Nx, Ny;
+  aniso(gx, gy, eps, kN6eps, as, Nx, Ny);
+  const double U = U0[i];
+  const double rho = rho0 ? rho0[i] : 1.0;
+  const double ux = ux0 ? ux0[i] : 0.0;
+  const double uy = uy0 ? uy0[i] : 0.0;
+  const double uu = ux * ux + uy * uy;
+  const long long o = (long long)Y * C.pitch + X;
+  float hv[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const double w = wd_of(a);
+    hv[a] = (float)(w * (ph - Dphi3 * cdot(a, Nx, Ny)));
+    pops[(PLANE_H + a) * C.plane + o] = hv[a];
+    const double cu = cdot(a, ux, uy);
+    pops[(PLANE_G + a) * C.plane + o] = (float)(w * U * (1.0 + 3.0 * cu));
+    if (FLOW)
+      pops[(PLANE_F + a) * C.plane + o] =
+          (float)(w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+  }
+  const float s = sum9(hv);
+  phi_cur[o] = s;
+  phi_prev[o] = s;
+}
+
+// phi = sum h of the current populations (after a checkpoint load).
+__global__ void phi_from_pops_kernel(const Consts C, const float* __restrict__ pops,
+                                     float* __restrict__ phi) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= C.nx || Y >= C.ny) return;
+  const long long o = (long long)Y * C.pitch + X;
+  float hv[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) hv[a] = pops[(PLANE_H + a) * C.plane + o];
+  phi[o] = sum9(hv);
+}
+
+// Moment of the current state into a contiguous [ny][nx] float array.
+// which: 0 phi, 1 U, 2 rho, 3 u*_x, 4 u*_y, 5 phi history.
+__global__ void moment_kernel(const Consts C, int which, int flow,
+                              const float* __restrict__ pops, const float* __restrict__ phi,
+                              const float* __restrict__ phi_prev, float* __restrict__ out) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= C.nx || Y >= C.ny) return;
+  const long long o = (long long)Y * C.pitch + X;
+  float r = 0.0f;
+  if (which == 0) {
+    r = phi[o];
+  } else if (which == 5) {
+    r = phi_prev[o];
+  } else if (which == 1) {
+    float v[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_G + a) * C.plane + o];
+    r = sum9(v);
+  } else if (!flow) {
+    r = which == 2 ? 1.0f : 0.0f;
+  } else {
+    float v[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_F + a) * C.plane + o];
+    const float rho = sum9(v);
+    if (which == 2) {
+      r = rho;
+    } else {
+      const float ph = phi[o];
+      const float onep = 1.0f + ph;
+      const float k = C.kdrag * rho * onep * onep * (1.0f - ph);
+      const float inv = 1.0f / (rho + 0.5f * k);
+      const float sfac = 0.5f * (1.0f - ph);
+      r = which == 3 ? sfac * (sumcx9(v) * inv) : sfac * (sumcy9(v) * inv);
+    }
+  }
+  out[(long long)Y * C.nx + X] = r;
+}
+
+constexpr int kStatThreads = 256;
+constexpr int kNStat = 5;
+
+// Block-level partial sums in double: solid area, mass, vapour invariant, sum phi, count of
+// non-finite nodes. One partial row per block; the final kernel adds rows in a fixed order,
+// so the result does not depend on scheduling.
+__global__ void __launch_bounds__(kStatThreads)
+    stats_partial_kernel(const Consts C, int flow, double area_w, double half_Lsat,
+                         const float* __restrict__ pops, const float* __restrict__ phi,
+                         const float* __restrict__ phi_prev, double* __restrict__ partial) {
+  double acc[kNStat] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const long long n = (long long)C.nx * C.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int Y = (int)(i / C.nx), X = (int)(i - (long long)Y * C.nx);
+    const long long o = (long long)Y * C.pitch + X;
+    const float ph = phi[o];
+    float v[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_G + a) * C.plane + o];
+    const float U = sum9(v);
+    float rho = 1.0f;
+    if (flow) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_F + a) * C.plane + o];
+      rho = sum9(v);
+    }
+    acc[0] += area_w * (1.0 + (double)ph);
+    acc[1] += (double)rho;
+    acc[2] += (double)U + half_Lsat * (double)phi_prev[o];
+    acc[3] += (double)ph;
+    acc[4] += (isfinite(ph) && isfinite(U) && isfinite(rho)) ? 0.0 : 1.0;
+  }
+  __shared__ double red[kNStat][kStatThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kNStat; ++k) {
+    double v = acc[k];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[k][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNStat) {
+    double s = 0.0;
+    for (int w = 0; w < kStatThreads / 32; ++w) s += red[threadIdx.x][w];
+    partial[(long long)blockIdx.x * kNStat + threadIdx.x] = s;
+  }
+}
+
+__global__ void stats_final_kernel(const double* __restrict__ partial, int nblocks,
+                                   double* __restrict__ out) {
+  if (threadIdx.x < kNStat) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(long long)b * kNStat + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+}  // namespace lbmice

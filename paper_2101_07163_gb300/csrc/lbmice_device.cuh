@@ -1,0 +1,133 @@
+// Device code of the coupled lattice-Boltzmann ice-crystal step (arXiv 2101.07163, Sec. 2.2)
+// for sm_103a: the fused collide-stream kernel over the three D2Q9 lattices, the
+// equilibrium initialisation, the moment export and the FP64 reductions.
+//
+// State layout in HBM (one allocation per buffer, row pitch padded to 32 floats = 128 B):
+//   populations: planes [h0..h8 | g0..g8 | f0..f8][ny][pitch] float, two buffers (pull
+//                scheme reads one and writes the other);
+//   phi:         three rotating [ny][pitch] float planes holding phi^{n-1}, phi^n, phi^{n+1}
+//                (phi^n feeds the E4 gradient with a two-node halo, phi^{n-1} the d(phi)/dt
+//                of the vapour source, phi^{n+1} = sum h^{n+1} is written by the step).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmice {
+
+// ---- D2Q9 (directions are compile-time after unrolling) ---------------------------------
+__host__ __device__ constexpr int cx_of(int a) {
+  return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy_of(int a) {
+  return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr float w_of(int a) {
+  return a == 0 ? 4.0f / 9.0f : (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+__host__ __device__ constexpr double wd_of(int a) {
+  return a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+// direction index after reflecting c_x (mirror across a vertical wall) or c_y
+__host__ __device__ constexpr int mirx_of(int a) {
+  return a == 1 ? 3 : a == 3 ? 1 : a == 5 ? 6 : a == 6 ? 5 : a == 7 ? 8 : a == 8 ? 7 : a;
+}
+__host__ __device__ constexpr int miry_of(int a) {
+  return a == 2 ? 4 : a == 4 ? 2 : a == 5 ? 8 : a == 8 ? 5 : a == 6 ? 7 : a == 7 ? 6 : a;
+}
+
+// c_a . v built from additions and exact negations only, so the mirror image of a state
+// produces bit-identical projections.
+template <class T>
+__device__ __forceinline__ T cdot(int a, T vx, T vy) {
+  const int cx = cx_of(a), cy = cy_of(a);
+  if (cx == 0) return cy > 0 ? vy : (cy < 0 ? -vy : T(0));
+  const T r = cx > 0 ? vx : -vx;
+  if (cy == 0) return r;
+  return cy > 0 ? r + vy : r - vy;
+}
+
+// Sums over the nine directions grouped by opposite pairs; invariant under every
+// reflection of the square, which keeps mirror-symmetric states bit-exactly symmetric.
+template <class T>
+__device__ __forceinline__ T sum9(const T* v) {
+  return v[0] + (((v[1] + v[3]) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8])));
+}
+template <class T>
+__device__ __forceinline__ T sumcx9(const T* v) {
+  return (v[1] - v[3]) + ((v[5] - v[7]) + (v[8] - v[6]));
+}
+template <class T>
+__device__ __forceinline__ T sumcy9(const T* v) {
+  return (v[2] - v[4]) + ((v[5] - v[7]) + (v[6] - v[8]));
+}
+
+enum : int { BC_PERIODIC = 0, BC_INLET = 1, BC_OUTLET = 2, BC_FREESLIP = 3 };
+enum : int { PLANE_H = 0, PLANE_G = 9, PLANE_F = 18 };
+
+// Lattice constants of one grid, precomputed on the host (lattice units).
+struct Consts {
+  int nx, ny, pitch;
+  int bc[4];
+  long long plane;   // floats per population plane: pitch * ny
+  float Dphi3;       // 3 (W0^2/tau0) dt/dx^2: eta = Dphi3 a_s^2 + 1/2, h^eq flux weight
+  float dt_tau0;     // dt/tau0: weight of the phase-field source Q
+  float lambda;      // coupling of U into Q
+  float Dlat3;       // 3 D dt/dx^2: tau_g = Dlat3 q + 1/2
+  float half_Lsat;   // L_sat / 2
+  float eps;         // six-fold anisotropy strength
+  float kN6eps;      // kappa_N * 6 eps: N = kN6eps a_s sin(6 theta) (g_y, -g_x)
+  float kdrag;       // h nu / (4 (W0/dx)^2): k = kdrag rho (1+phi)^2 (1-phi)
+  float inv_tau_f;   // 1 / tau_f
+  float guo;         // 1 - 1/(2 tau_f)
+  float U_in;        // inlet supersaturation
+  float uin_x[4], uin_y[4];  // inlet velocity of each face (inward normal times u_in)
+};
+
+// E4 gradient weights (Table 1): shells |c|^2 = 1 and 2.
+__device__ constexpr float kW1 = 1.0f / 3.0f;
+__device__ constexpr float kW2 = 1.0f / 12.0f;
+
+// Six-fold anisotropy from a lattice gradient (Sec. 2.1): a_s = 1 + eps cos(6 theta) and the
+// anisotropic flux N = kappa_N a_s 6 eps sin(6 theta) (g_y, -g_x). cos/sin(6 theta) are the
+// real/imaginary parts of (n_x + i n_y)^6 of the unit normal; |g|^2 <= 1e-12 -> isotropic.
+template <class T>
+__device__ __forceinline__ void aniso(T gx, T gy, T eps, T kN6eps, T& as, T& Nx, T& Ny) {
+  const T s = gx * gx + gy * gy;
+  as = T(1);
+  Nx = T(0);
+  Ny = T(0);
+  if (s > T(1e-12)) {
+    const T rinv = T(1) / sqrt(s);
+    const T nx = gx * rinv, ny = gy * rinv;
+    const T X = nx * nx, Y = ny * ny;
+    const T cos6 = X * X * X - T(15) * X * X * Y + T(15) * X * Y * Y - Y * Y * Y;
+    const T sin6 = nx * ny * (T(6) * X * X - T(20) * X * Y + T(6) * Y * Y);
+    as = T(1) + eps * cos6;
+    const T t = kN6eps * as * sin6;
+    Nx = t * gy;
+    Ny = -(t * gx);
+  }
+}
+
+// Ghost resolution of one axis for phi reads (R: periodic wrap, zero-gradient clamp,
+// free-slip reflection about the wall half a cell out, inlet = vapour). Returns false for
+// an inlet ghost. Valid for coordinates up to two cells outside.
+__device__ __forceinline__ bool axis_phi(int v, int n, int bc_lo, int bc_hi, int& out) {
+  if (v < 0) {
+    if (bc_lo == BC_PERIODIC) { out = v + n; return true; }
+    if (bc_lo == BC_OUTLET) { out = 0; return true; }
+    if (bc_lo == BC_FREESLIP) { out = -1 - v; return true; }
+    return false;
+  }
+  if (v >= n) {
+    if (bc_hi == BC_PERIODIC) { out = v - n; return true; }
+    if (bc_hi == BC_OUTLET) { out = n - 1; return true; }
+    if (bc_hi == BC_FREESLIP) { out = 2 * n - 1 - v; return true; }
+    return false;
+  }
+  out = v;
+  return true;
+}
+
+}  // namespace lbmice

@@ -1,0 +1,254 @@
+// The fused collide-stream kernel: one launch advances h, g and f by one time step
+// (arXiv 2101.07163, Sec. 2.2.1-2.2.3) over the whole grid.
+//
+// Each CTA owns a TX x TY tile of destination nodes and works in three phases:
+//   A. phi^n of the tile plus a two-node halo (ghosts resolved) -> shared memory;
+//   B. every source node of the tile plus a one-node halo is collided once: moments, the
+//      E4 gradient from the shared phi tile, a_s and the anisotropic flux, the drag, and the
+//      27 post-collision populations, which go to shared memory (h already divided by
+//      a_s^2, together with 1 - 1/a_s^2, so the pull of Eq. (d) is one FMA). Interior nodes
+//      keep their own pre-collision h in registers;
+//   C. each destination pulls its 27 populations from the shared tile, applies Eq. (d),
+//      writes h, g, f and phi^{n+1} = sum h to HBM.
+// Global loads and stores of phases B and C are row-coalesced (consecutive threads own
+// consecutive x). HBM traffic per node: 27 populations in and out, phi^n, phi^{n-1} in,
+// phi^{n+1} out; halo re-reads hit L2.
+#pragma once
+
+#include "lbmice_device.cuh"
+
+namespace lbmice {
+
+struct StepPtrs {
+  const float* __restrict__ pin;      // populations at time n
+  float* __restrict__ pout;           // populations at time n + 1
+  const float* __restrict__ phi_n;    // phi^n
+  const float* __restrict__ phi_nm1;  // phi^{n-1}
+  float* __restrict__ phi_np1;        // phi^{n+1}
+};
+
+template <int TX, int TY>
+struct Tile {
+  static constexpr int PW = TX + 4;                  // phi tile row (halo 2)
+  static constexpr int PN = PW * (TY + 4);
+  static constexpr int SW = TX + 2;                  // source tile row (halo 1)
+  static constexpr int SN = SW * (TY + 2);
+  static constexpr int NRING = SN - TX * TY;
+  static constexpr int NT = TX * TY;
+  template <bool FLOW>
+  static constexpr size_t smem_bytes() {
+    return sizeof(float) * (size_t)(PN + (FLOW ? 27 : 18) * SN + SN);
+  }
+};
+
+// Collide the source node at tile position (sx, sy) in [0, TX+2) x [0, TY+2), global
+// coordinates (X, Y) in [-1, nx] x [-1, ny], and store its post-collision populations.
+// Ghost positions take the collision of the node their face rule maps them to (directions
+// mirrored across a free-slip wall), or the fixed inlet state.
+template <int TX, int TY, bool FLOW, bool OWN>
+__device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& P, int X, int Y,
+                                               int sx, int sy, const float* __restrict__ sphi,
+                                               float* __restrict__ spost,
+                                               float* __restrict__ sB, float* hown) {
+  using T = Tile<TX, TY>;
+  const int node = sy * T::SW + sx;
+  int mx = X, my = Y, lx = sx, ly = sy;
+  bool mirx = false, miry = false;
+  int inlet = -1;
+  if (X < 0 || X >= C.nx) {
+    const int face = X < 0 ? 0 : 1;
+    const int bc = X < 0 ? C.bc[0] : C.bc[1];
+    if (bc == BC_PERIODIC) {
+      mx = X < 0 ? X + C.nx : X - C.nx;
+    } else {
+      mx = X < 0 ? 0 : C.nx - 1;
+      lx += X < 0 ? 1 : -1;
+      mirx = bc == BC_FREESLIP;
+      if (bc == BC_INLET) inlet = face;
+    }
+  }
+  if (Y < 0 || Y >= C.ny) {
+    const int face = Y < 0 ? 2 : 3;
+    const int bc = Y < 0 ? C.bc[2] : C.bc[3];
+    if (bc == BC_PERIODIC) {
+      my = Y < 0 ? Y + C.ny : Y - C.ny;
+    } else {
+      my = Y < 0 ? 0 : C.ny - 1;
+      ly += Y < 0 ? 1 : -1;
+      miry = bc == BC_FREESLIP;
+      if (bc == BC_INLET && inlet < 0) inlet = face;
+    }
+  }
+  const long long idx = (long long)my * C.pitch + mx;
+  const float* __restrict__ pin = P.pin + idx;
+
+  if (inlet >= 0) {
+    // Inlet ghost: vapour at the inlet state, flow equilibrium at the adjacent density.
+    const float ux = inlet == 0 ? C.uin_x[0] : inlet == 1 ? C.uin_x[1]
+                   : inlet == 2 ? C.uin_x[2] : C.uin_x[3];
+    const float uy = inlet == 0 ? C.uin_y[0] : inlet == 1 ? C.uin_y[1]
+                   : inlet == 2 ? C.uin_y[2] : C.uin_y[3];
+    float rho = 1.0f;
+    if (FLOW) {
+      float fv[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) fv[a] = __ldg(pin + (PLANE_F + a) * C.plane);
+      rho = sum9(fv);
+    }
+    const float uu = ux * ux + uy * uy;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const float cu = cdot(a, ux, uy);
+      spost[(PLANE_H + a) * T::SN + node] = -w_of(a);
+      spost[(PLANE_G + a) * T::SN + node] = w_of(a) * C.U_in * (1.0f + 3.0f * cu);
+      if (FLOW)
+        spost[(PLANE_F + a) * T::SN + node] =
+            w_of(a) * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+    }
+    sB[node] = 0.0f;
+    return;
+  }
+
+  // ---- moments at time n (Sec. 2.2) ----
+  float hv[9], gv[9], fv[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    hv[a] = __ldg(pin + (PLANE_H + a) * C.plane);
+    gv[a] = __ldg(pin + (PLANE_G + a) * C.plane);
+    if (FLOW) fv[a] = __ldg(pin + (PLANE_F + a) * C.plane);
+  }
+  const float php = __ldg(P.phi_nm1 + idx);
+  const int pc = (ly + 1) * T::PW + (lx + 1);
+  const float ph = sphi[pc];
+  const float U = sum9(gv);
+  float rho = 1.0f, jx = 0.0f, jy = 0.0f;
+  if (FLOW) {
+    rho = sum9(fv);
+    jx = sumcx9(fv);
+    jy = sumcy9(fv);
+  }
+
+  // ---- E4 gradient of phi (Sec. 3.1.1, Table 1) and anisotropy (Sec. 2.1) ----
+  const float pE = sphi[pc + 1], pW = sphi[pc - 1];
+  const float pN = sphi[pc + T::PW], pS = sphi[pc - T::PW];
+  const float pNE = sphi[pc + T::PW + 1], pNW = sphi[pc + T::PW - 1];
+  const float pSE = sphi[pc - T::PW + 1], pSW = sphi[pc - T::PW - 1];
+  const float gx = kW1 * (pE - pW) + kW2 * ((pNE - pNW) + (pSE - pSW));
+  const float gy = kW1 * (pN - pS) + kW2 * ((pNE - pSE) + (pNW - pSW));
+  float as, Nx, Ny;
+  aniso(gx, gy, C.eps, C.kN6eps, as, Nx, Ny);
+  const float as2 = as * as;
+  const float inv_as2 = 1.0f / as2;
+  const float inv_eta = 1.0f / (C.Dphi3 * as2 + 0.5f);
+  const float omp2 = 1.0f - ph * ph;
+  const float srcQ = (ph - ph * ph * ph + C.lambda * U * omp2 * omp2) * C.dt_tau0;
+
+  // ---- flow velocity with solid damping (Sec. 2.2.1) ----
+  float usx = 0.0f, usy = 0.0f, k = 0.0f;
+  if (FLOW) {
+    const float onep = 1.0f + ph;
+    k = C.kdrag * rho * onep * onep * (1.0f - ph);
+    const float inv = 1.0f / (rho + 0.5f * k);
+    const float sfac = 0.5f * (1.0f - ph);
+    usx = sfac * (jx * inv);
+    usy = sfac * (jy * inv);
+  }
+  // ---- vapour relaxation and source (Sec. 2.2.2) ----
+  const float q = fminf(fmaxf(1.0f - ph, 0.0f), 2.0f);
+  const float inv_tg = 1.0f / (C.Dlat3 * q + 0.5f);
+  const float srcU = -C.half_Lsat * (ph - php);
+
+  if (OWN) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) hown[a] = hv[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    int am = mirx ? mirx_of(a) : a;
+    am = miry ? miry_of(am) : am;
+    const float w = w_of(a);
+    // phase field, Eq. (d)/(e): h* = h - (h - h^eq)/eta + w Q dt/tau0; stored as h*/a_s^2
+    const float heq = w * (ph - C.Dphi3 * cdot(a, Nx, Ny));
+    const float hs = hv[a] - (hv[a] - heq) * inv_eta + w * srcQ;
+    spost[(PLANE_H + am) * T::SN + node] = hs * inv_as2;
+    // vapour: g* = g - (g - g^eq)/tau_g + w S dt, g^eq = w U (1 + 3 c.u*)
+    const float cu = cdot(a, usx, usy);
+    const float geq = w * U * (1.0f + 3.0f * cu);
+    spost[(PLANE_G + am) * T::SN + node] = gv[a] - (gv[a] - geq) * inv_tg + w * srcU;
+    if (FLOW) {
+      // flow: BGK to f^eq(rho, u*) plus Guo forcing of F = -k u*
+      const float Fx = -k * usx, Fy = -k * usy;
+      const float uF = usx * Fx + usy * Fy;
+      const float uu = usx * usx + usy * usy;
+      const float cF = cdot(a, Fx, Fy);
+      const float feq = w * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+      const float force = C.guo * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
+      spost[(PLANE_F + am) * T::SN + node] = fv[a] - (fv[a] - feq) * C.inv_tau_f + force;
+    }
+  }
+  sB[node] = 1.0f - inv_as2;
+}
+
+template <int TX, int TY, bool FLOW>
+__global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const StepPtrs P) {
+  using T = Tile<TX, TY>;
+  extern __shared__ float smem[];
+  float* sphi = smem;
+  float* spost = sphi + T::PN;
+  float* sB = spost + (FLOW ? 27 : 18) * T::SN;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+
+  // ---- A: phi^n with a two-node halo ----
+  for (int i = tid; i < T::PN; i += T::NT) {
+    const int lx = i % T::PW, ly = i / T::PW;
+    const int X = x0 - 2 + lx, Y = y0 - 2 + ly;
+    int gx, gy;
+    float v = -1.0f;
+    if (X > C.nx + 1 || Y > C.ny + 1) {
+      v = 0.0f;  // beyond the grid's two-node halo (ragged last tile): never read
+    } else if (axis_phi(X, C.nx, C.bc[0], C.bc[1], gx) &&
+               axis_phi(Y, C.ny, C.bc[2], C.bc[3], gy)) {
+      v = __ldg(P.phi_n + (long long)gy * C.pitch + gx);
+    }
+    sphi[i] = v;
+  }
+  __syncthreads();
+
+  // ---- B: collide the tile (own node per thread) and its one-node ring ----
+  float hown[9];
+  {
+    const int X = x0 + tx, Y = y0 + ty;
+    if (X <= C.nx && Y <= C.ny)
+      collide_source<TX, TY, FLOW, true>(C, P, X, Y, tx + 1, ty + 1, sphi, spost, sB, hown);
+  }
+  for (int r = tid; r < T::NRING; r += T::NT) {
+    // ring order: bottom row, top row, then left and right columns
+    int sx, sy;
+    if (r < T::SW) { sx = r; sy = 0; }
+    else if (r < 2 * T::SW) { sx = r - T::SW; sy = TY + 1; }
+    else { const int k = r - 2 * T::SW; sy = 1 + (k >> 1); sx = (k & 1) ? TX + 1 : 0; }
+    const int X = x0 - 1 + sx, Y = y0 - 1 + sy;
+    if (X >= -1 && X <= C.nx && Y >= -1 && Y <= C.ny)
+      collide_source<TX, TY, FLOW, false>(C, P, X, Y, sx, sy, sphi, spost, sB, nullptr);
+  }
+  __syncthreads();
+
+  // ---- C: pull, Eq. (d) for h, write populations and phi^{n+1} ----
+  const int X = x0 + tx, Y = y0 + ty;
+  if (X >= C.nx || Y >= C.ny) return;
+  const long long idx = (long long)Y * C.pitch + X;
+  float hn[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const int src = (ty + 1 - cy_of(a)) * T::SW + (tx + 1 - cx_of(a));
+    hn[a] = fmaf(hown[a], sB[src], spost[(PLANE_H + a) * T::SN + src]);
+    P.pout[(PLANE_H + a) * C.plane + idx] = hn[a];
+    P.pout[(PLANE_G + a) * C.plane + idx] = spost[(PLANE_G + a) * T::SN + src];
+    if (FLOW) P.pout[(PLANE_F + a) * C.plane + idx] = spost[(PLANE_F + a) * T::SN + src];
+  }
+  P.phi_np1[idx] = sum9(hn);
+}
+
+}  // namespace lbmice

@@ -1,0 +1,227 @@
+"""Thin Python binding of the C ABI in include/lbmice.h (ctypes; argument marshalling only).
+
+Every step of the solver runs in the CUDA kernels of liblbmice.so. PyTorch supplies the
+CUDA stream and, where the caller wants device results, the device memory. There is no
+CPU fallback: constructing a :class:`Lattice` without the built library or without a GPU
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+OK, EINVAL, ECUDA, ENOMEM, ENONFINITE, EUNSTABLE, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FREESLIP = 0, 1, 2, 3
+PHI, U, RHO, UX, UY, PHI_PREV, POPS = 0, 1, 2, 3, 4, 5, 6
+NSTATS = 6
+STAT_NAMES = ("area", "mass", "vapour_invariant", "sum_phi", "nonfinite", "steps")
+
+EXPORTS = ("lbmice_params_default", "lbmice_create", "lbmice_init_seed", "lbmice_set_fields",
+           "lbmice_step", "lbmice_fields", "lbmice_load", "lbmice_stats", "lbmice_sync",
+           "lbmice_steps_done", "lbmice_destroy", "lbmice_strerror")
+
+
+class LbmiceError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class Params(ctypes.Structure):
+    """Mirror of struct lbmice_params."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+        ("W0", ctypes.c_double), ("tau0", ctypes.c_double),
+        ("D", ctypes.c_double), ("lam", ctypes.c_double),
+        ("L_sat", ctypes.c_double), ("eps", ctypes.c_double),
+        ("kappa_N", ctypes.c_double),
+        ("U_in", ctypes.c_double), ("u_in", ctypes.c_double), ("nu", ctypes.c_double),
+        ("bc", ctypes.c_int32 * 4), ("flow", ctypes.c_int32),
+        ("check_every", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblbmice.so (built by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is not built; run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB)
+        vp, dp, i32, i64, sz = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t)
+        pp = ctypes.POINTER(Params)
+        L.lbmice_params_default.argtypes = [pp, i32, i32]
+        L.lbmice_create.argtypes = [pp, vp, ctypes.POINTER(vp)]
+        L.lbmice_init_seed.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double]
+        L.lbmice_set_fields.argtypes = [vp, vp, vp, vp, vp, vp, i32]
+        L.lbmice_step.argtypes = [vp, i64]
+        L.lbmice_fields.argtypes = [vp, i32, vp, sz, i32]
+        L.lbmice_load.argtypes = [vp, i32, vp, sz, i32]
+        L.lbmice_stats.argtypes = [vp, dp]
+        L.lbmice_sync.argtypes = [vp]
+        L.lbmice_steps_done.argtypes = [vp]
+        L.lbmice_steps_done.restype = i64
+        L.lbmice_destroy.argtypes = [vp]
+        L.lbmice_strerror.argtypes = [ctypes.c_int]
+        L.lbmice_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().lbmice_strerror(int(code)).decode()
+    except RuntimeError:
+        return "error"
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise LbmiceError(rc, what)
+
+
+def make_params(nx, ny, *, dx=0.4, dt=0.008, W0=1.0, tau0=1.0, D=2.0, lam=0.0, L_sat=1.0,
+                eps=0.05, kappa_N=1.0, U_in=0.0, u_in=0.0, nu=0.016,
+                bc=(BC_PERIODIC,) * 4, flow=False, check_every=0) -> Params:
+    p = Params()
+    _check(lib().lbmice_params_default(ctypes.byref(p), int(nx), int(ny)), "params_default")
+    p.dx, p.dt, p.W0, p.tau0 = dx, dt, W0, tau0
+    p.D, p.lam, p.L_sat, p.eps, p.kappa_N = D, lam, L_sat, eps, kappa_N
+    p.U_in, p.u_in, p.nu = U_in, u_in, nu
+    for i in range(4):
+        p.bc[i] = int(bc[i])
+    p.flow = 1 if flow else 0
+    p.check_every = int(check_every)
+    return p
+
+
+def _ptr_host(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Lattice:
+    """One grid of the coupled ice-growth solver on the current CUDA device.
+
+    ``stream``: a torch.cuda.Stream (default: the current stream). Keyword parameters are
+    those of :func:`make_params`.
+    """
+
+    def __init__(self, nx: int, ny: int, *, stream=None, **params):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("lbmice needs a CUDA GPU; there is no CPU fallback")
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = make_params(nx, ny, **params)
+        self.flow = bool(self.params.flow)
+        self.nplanes = 27 if self.flow else 18
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = self._stream.device
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().lbmice_create(ctypes.byref(self.params),
+                                       ctypes.c_void_p(self._stream.cuda_stream),
+                                       ctypes.byref(h)), "lbmice_create")
+        self._h = h
+
+    # -- lifetime -------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().lbmice_destroy(self._h), "lbmice_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def stream(self):
+        return self._stream
+
+    # -- initial conditions ---------------------------------------------------------------
+    def init_seed(self, cx: float, cy: float, R0: float, U0: float):
+        _check(lib().lbmice_init_seed(self._h, cx, cy, R0, U0), "lbmice_init_seed")
+
+    def set_fields(self, phi, U, rho=None, ux=None, uy=None):
+        """Moment fields of shape (ny, nx): numpy arrays (host) or float64 CUDA tensors."""
+        import torch
+        arrs = [phi, U, rho, ux, uy]
+        if isinstance(phi, torch.Tensor):
+            ts = [None if a is None else a.to(self.device, torch.float64).contiguous()
+                  for a in arrs]
+            for t in ts:
+                if t is not None and tuple(t.shape) != (self.ny, self.nx):
+                    raise ValueError("fields must have shape (ny, nx)")
+            ptrs = [None if t is None else ctypes.c_void_p(t.data_ptr()) for t in ts]
+            _check(lib().lbmice_set_fields(self._h, *ptrs, 1), "lbmice_set_fields")
+            self._keep = ts
+            return
+        ns = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+        for a in ns:
+            if a is not None and a.shape != (self.ny, self.nx):
+                raise ValueError("fields must have shape (ny, nx)")
+        _check(lib().lbmice_set_fields(self._h, *[_ptr_host(a) for a in ns], 0),
+               "lbmice_set_fields")
+
+    # -- time stepping --------------------------------------------------------------------
+    def step(self, n: int = 1):
+        _check(lib().lbmice_step(self._h, int(n)), "lbmice_step")
+
+    @property
+    def steps_done(self) -> int:
+        return int(lib().lbmice_steps_done(self._h))
+
+    def sync(self):
+        _check(lib().lbmice_sync(self._h), "lbmice_sync")
+
+    # -- outputs --------------------------------------------------------------------------
+    def field(self, which: int, out=None):
+        """One moment field as float32. ``out`` may be a CUDA tensor (asynchronous);
+        without it a host numpy array is returned."""
+        if out is not None:
+            if out.numel() * 4 < self.nx * self.ny or out.dtype.itemsize != 4:
+                raise ValueError("out must be a float32 tensor of nx*ny elements")
+            _check(lib().lbmice_fields(self._h, int(which), ctypes.c_void_p(out.data_ptr()),
+                                       out.numel() * 4, 1), "lbmice_fields")
+            return out
+        a = np.empty((self.ny, self.nx), dtype=np.float32)
+        _check(lib().lbmice_fields(self._h, int(which), _ptr_host(a), a.nbytes, 0),
+               "lbmice_fields")
+        return a
+
+    def pops(self) -> np.ndarray:
+        """Raw populations (18 or 27, ny, nx): planes h0..h8, g0..g8[, f0..f8]."""
+        a = np.empty((self.nplanes, self.ny, self.nx), dtype=np.float32)
+        _check(lib().lbmice_fields(self._h, POPS, _ptr_host(a), a.nbytes, 0), "lbmice_fields")
+        return a
+
+    def load(self, which: int, arr: np.ndarray):
+        a = np.ascontiguousarray(arr, dtype=np.float32)
+        _check(lib().lbmice_load(self._h, int(which), _ptr_host(a), a.nbytes, 0),
+               "lbmice_load")
+
+    def stats(self) -> dict:
+        out = (ctypes.c_double * NSTATS)()
+        _check(lib().lbmice_stats(self._h, out), "lbmice_stats")
+        return dict(zip(STAT_NAMES, list(out)))

@@ -1,0 +1,300 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on the same seeded inputs.
+
+Tolerances (FP32 arithmetic against FP64; values are O(1)):
+  - one step, every population: 1e-6 absolute (a few FP32 ulps of the O(0.1-1) populations);
+  - up to 200 steps, moments: 2e-5;
+  - 2000 steps of the 128 x 128 seed: 1e-4 for phi and U.
+The accumulated error grows roughly like sqrt(n) times the per-step rounding (~1e-7), with
+extra growth at the moving interface; these bounds leave a factor of a few over that.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import LAT_F, LAT_G, LAT_H
+from paper_2101_07163_gb300 import lbmice
+from paper_2101_07163_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CHANNEL_X = (W.BC_INLET, W.BC_OUTLET, W.BC_FREESLIP, W.BC_FREESLIP)
+CHANNEL_Y = (W.BC_PERIODIC, W.BC_PERIODIC, W.BC_INLET, W.BC_OUTLET)
+BOXES = {
+    "periodic": (W.BC_PERIODIC,) * 4,
+    "channel_x": CHANNEL_X,
+    "channel_y": CHANNEL_Y,
+    "walls": (W.BC_FREESLIP,) * 4,
+    "outlets": (W.BC_OUTLET, W.BC_OUTLET, W.BC_OUTLET, W.BC_FREESLIP),
+    "inlet_plus_x": (W.BC_OUTLET, W.BC_INLET, W.BC_FREESLIP, W.BC_OUTLET),
+}
+
+
+def pair(w: W.Workload, fields: dict):
+    lat = lbmice.Lattice(w.nx, w.ny, **w.params())
+    lat.set_fields(**fields)
+    orc = oracle.Oracle(nx=w.nx, ny=w.ny, **w.params())
+    orc.set_fields(**fields)
+    return lat, orc
+
+
+def maxdiff(a, b):
+    return float(np.abs(np.asarray(a, dtype=np.float64) - b).max())
+
+
+def compare_pops(lat, orc, tol):
+    p = lat.pops().astype(np.float64)
+    assert maxdiff(p[0:9], orc.pops(LAT_H)) < tol
+    assert maxdiff(p[9:18], orc.pops(LAT_G)) < tol
+    if orc.flow:
+        assert maxdiff(p[18:27], orc.pops(LAT_F)) < tol
+
+
+def compare_moments(lat, orc, tol):
+    for which in (lbmice.PHI, lbmice.U, lbmice.RHO, lbmice.UX, lbmice.UY, lbmice.PHI_PREV):
+        d = maxdiff(lat.field(which), orc.field(which))
+        assert d < tol, (which, d)
+
+
+def channel_workload(name, nx, ny, bc, **kw):
+    return W.Workload(name, nx, ny, 1, flow=True, eps=0.08, D=2.0, U0=0.3, U_in=0.25,
+                      u_in=0.03, nu=0.05, bc=bc, cx=nx * 0.4, cy=ny * 0.55, R0=7.0, **kw)
+
+
+# ---- one step, every population, ragged grids (tiles of 32 x 8 with a tail) ----------------
+
+@pytest.mark.parametrize("box", sorted(BOXES))
+def test_one_step_every_population(box):
+    w = channel_workload(box, 100, 76, BOXES[box])
+    lat, orc = pair(w, W.perturbed_fields(w, 7, amp_phi=0.3, amp_u=0.02))
+    compare_pops(lat, orc, 1e-6)  # the initial equilibria
+    lat.step(1)
+    orc.step(1)
+    compare_pops(lat, orc, 1e-6)
+    compare_moments(lat, orc, 1e-6)
+
+
+@pytest.mark.parametrize("box", sorted(BOXES))
+def test_short_horizon_moments(box):
+    w = channel_workload(box, 70, 44, BOXES[box])
+    lat, orc = pair(w, W.perturbed_fields(w, 8, amp_phi=0.2, amp_u=0.01))
+    lat.step(200)
+    orc.step(200)
+    compare_moments(lat, orc, 2e-5)
+
+
+def test_phase_field_and_vapour_only():
+    w = W.C1.with_size(72, 60)
+    lat, orc = pair(w, W.perturbed_fields(w, 9))
+    lat.step(1)
+    orc.step(1)
+    compare_pops(lat, orc, 1e-6)
+    lat.step(199)
+    orc.step(199)
+    compare_moments(lat, orc, 2e-5)
+
+
+def test_small_and_degenerate_grids():
+    # smallest legal grid, single-tile grids, grids narrower than one tile
+    for nx, ny in [(4, 4), (5, 9), (33, 4), (31, 7)]:
+        w = channel_workload("tiny", nx, ny, (W.BC_PERIODIC,) * 4)
+        w.R0 = 1.5
+        lat, orc = pair(w, W.perturbed_fields(w, 10))
+        lat.step(3)
+        orc.step(3)
+        compare_pops(lat, orc, 1e-6)
+        w2 = channel_workload("tiny", nx, ny, CHANNEL_X)
+        w2.R0 = 1.5
+        lat, orc = pair(w2, W.perturbed_fields(w2, 11))
+        lat.step(3)
+        orc.step(3)
+        compare_pops(lat, orc, 1e-6)
+
+
+def test_uniform_vapour_is_a_fixed_point():
+    # phi = -1 everywhere: Q = 0, the vapour and phase field stay put exactly (edge case).
+    w = channel_workload("uniform", 64, 40, (W.BC_PERIODIC,) * 4)
+    f = dict(phi=np.full((40, 64), -1.0), U=np.full((40, 64), 0.3))
+    lat, _ = pair(w, f)
+    lat.step(50)
+    assert np.all(lat.field(lbmice.PHI) == np.float32(-1.0))
+    assert maxdiff(lat.field(lbmice.U), 0.3) < 1e-7
+
+
+# ---- the configurations of the workloads --------------------------------------------------
+
+def test_seed_128_periodic_2000_steps():
+    w = W.C1
+    f = W.seed_fields(w)
+    lat, orc = pair(w, f)
+    lat.step(w.steps)
+    orc.step(w.steps)
+    dphi = maxdiff(lat.field(lbmice.PHI), orc.field(oracle.PHI))
+    dU = maxdiff(lat.field(lbmice.U), orc.field(oracle.U))
+    assert dphi < 1e-4 and dU < 1e-4, (dphi, dU)
+
+
+def test_ventilated_512x384_full_size():
+    w = W.C2
+    lat, orc = pair(w, W.seed_fields(w))
+    lat.step(1)
+    orc.step(1)
+    compare_pops(lat, orc, 1e-6)
+    lat.step(49)
+    orc.step(49)
+    compare_moments(lat, orc, 2e-5)
+
+
+@pytest.mark.slow
+def test_plate_2048_full_size_two_steps():
+    # Full-size grid in the launch configuration the benchmark times, two steps from a
+    # perturbed seed so every node is non-trivial; the oracle computes every node.
+    w = W.C3
+    f = W.perturbed_fields(w, 12, amp_phi=0.05, amp_u=0.01)
+    lat, orc = pair(w, f)
+    lat.step(2)
+    orc.step(2)
+    compare_moments(lat, orc, 2e-6)
+    p = lat.pops()
+    rng = np.random.Generator(np.random.PCG64(3))
+    rows = np.concatenate([[0, 1, w.ny - 1], rng.integers(0, w.ny, 29)])
+    h = orc.pops(LAT_H)
+    assert maxdiff(p[0:9][:, rows], h[:, rows]) < 1e-6
+    del h
+    fo = orc.pops(LAT_F)
+    assert maxdiff(p[18:27][:, rows], fo[:, rows]) < 1e-6
+
+
+def test_ventilation_upstream_tip_grows_faster():
+    # Sec. 3.1.3 / Sec. 3.2.2 on the 512 x 384 channel: the tip facing the inflow is ahead.
+    w = W.C2
+    lat = lbmice.Lattice(w.nx, w.ny, **w.params())
+    lat.init_seed(w.cx, w.cy, w.R0, w.U0)
+    lat.step(8000)
+    phi = lat.field(lbmice.PHI).astype(np.float64)
+    from tests.helpers import tip_x
+    up = w.cx - tip_x(phi, w.cy, w.cx, -1)
+    down = tip_x(phi, w.cy, w.cx, +1) - w.cx
+    assert np.isfinite(up) and np.isfinite(down)
+    assert up > down + 1.0, (up, down)
+
+
+# ---- invariants, symmetry, determinism ----------------------------------------------------
+
+def test_mirror_symmetry_bit_exact_on_gpu():
+    w = W.Workload("m", 96, 64, 1, flow=True, eps=0.07, nu=0.05)
+    f = W.mirror_fields(w, 21, amp=0.2)
+    lat = lbmice.Lattice(w.nx, w.ny, **w.params())
+    lat.set_fields(**f)
+    lat.step(300)
+    ix, iy = (-np.arange(w.nx)) % w.nx, (-np.arange(w.ny)) % w.ny
+    for which in (lbmice.PHI, lbmice.U, lbmice.RHO):
+        a = lat.field(which)
+        np.testing.assert_array_equal(a, a[:, ix])
+        np.testing.assert_array_equal(a, a[iy, :])
+    ux = lat.field(lbmice.UX)
+    np.testing.assert_array_equal(ux, -ux[:, ix])
+
+
+def test_graph_replay_equals_single_launches():
+    w = channel_workload("g", 80, 48, CHANNEL_X)
+    f = W.perturbed_fields(w, 13)
+    a = lbmice.Lattice(w.nx, w.ny, **w.params())
+    b = lbmice.Lattice(w.nx, w.ny, **w.params())
+    a.set_fields(**f)
+    b.set_fields(**f)
+    a.step(125)              # two graph replays of 60 steps and five single steps
+    for _ in range(125):
+        b.step(1)
+    np.testing.assert_array_equal(a.pops(), b.pops())
+    np.testing.assert_array_equal(a.field(lbmice.PHI_PREV), b.field(lbmice.PHI_PREV))
+
+
+def test_checkpoint_resume_is_bit_exact():
+    w = channel_workload("c", 64, 40, CHANNEL_X)
+    f = W.perturbed_fields(w, 14)
+    a = lbmice.Lattice(w.nx, w.ny, **w.params())
+    a.set_fields(**f)
+    a.step(37)
+    pops, prev = a.pops(), a.field(lbmice.PHI_PREV)
+    a.step(71)
+    b = lbmice.Lattice(w.nx, w.ny, **w.params())
+    b.set_fields(**f)       # any state; overwritten below
+    b.step(5)
+    b.load(lbmice.POPS, pops)
+    b.load(lbmice.PHI_PREV, prev)
+    b.step(71)
+    np.testing.assert_array_equal(a.pops(), b.pops())
+
+
+def test_stats_match_oracle_reductions():
+    w = channel_workload("s", 90, 70, (W.BC_PERIODIC,) * 4, L_sat=1.3)
+    f = W.perturbed_fields(w, 15)
+    lat, orc = pair(w, f)
+    s0 = lat.stats()
+    lat.step(40)
+    orc.step(40)
+    s = lat.stats()
+    phi, U, rho, prev = (orc.field(k) for k in (oracle.PHI, oracle.U, oracle.RHO,
+                                                 oracle.PHI_PREV))
+    assert s["area"] == pytest.approx((0.5 * (1 + phi)).sum() * w.dx ** 2, rel=1e-6)
+    assert s["mass"] == pytest.approx(rho.sum(), rel=1e-7)
+    assert s["vapour_invariant"] == pytest.approx((U + 0.65 * prev).sum(), rel=1e-6)
+    assert s["sum_phi"] == pytest.approx(phi.sum(), rel=1e-5, abs=1e-3)
+    assert s["nonfinite"] == 0 and s["steps"] == 40
+    # exact invariants of the periodic grid hold on the GPU to FP32 rounding
+    assert s["mass"] == pytest.approx(s0["mass"], rel=1e-6)
+    assert s["vapour_invariant"] == pytest.approx(s0["vapour_invariant"], rel=1e-6)
+
+
+def test_nonfinite_state_is_reported_not_trapped():
+    w = channel_workload("n", 64, 40, (W.BC_PERIODIC,) * 4)
+    f = W.perturbed_fields(w, 16)
+    f["U"][20, 30] = np.nan
+    lat = lbmice.Lattice(w.nx, w.ny, check_every=1, **w.params())
+    lat.set_fields(**f)
+    with pytest.raises(lbmice.LbmiceError) as ei:
+        lat.step(5)
+    assert ei.value.code == lbmice.ENONFINITE
+    assert lat.stats()["nonfinite"] > 0
+    lat.sync()  # the context is still usable
+
+
+def test_init_seed_matches_workload_fields():
+    for w in (W.C1, W.C2.with_size(200, 120)):
+        lat = lbmice.Lattice(w.nx, w.ny, **w.params())
+        lat.init_seed(w.cx, w.cy, w.R0, w.U0)
+        ref, _ = pair(w, W.seed_fields(w))
+        for which in (lbmice.PHI, lbmice.U, lbmice.RHO, lbmice.UX):
+            assert maxdiff(lat.field(which), ref.field(which)) < 1e-6
+
+
+def test_device_fields_equal_host_fields():
+    import torch
+    w = channel_workload("d", 48, 40, CHANNEL_Y)
+    f = W.perturbed_fields(w, 17)
+    a = lbmice.Lattice(w.nx, w.ny, **w.params())
+    a.set_fields(**f)
+    b = lbmice.Lattice(w.nx, w.ny, **w.params())
+    b.set_fields(**{k: torch.from_numpy(v).cuda() for k, v in f.items()})
+    b.sync()
+    np.testing.assert_array_equal(a.pops(), b.pops())
+    out = torch.empty(w.ny, w.nx, device="cuda", dtype=torch.float32)
+    a.field(lbmice.PHI, out=out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), a.field(lbmice.PHI))
+
+
+def test_bad_buffer_sizes_are_rejected():
+    w = channel_workload("b", 32, 16, (W.BC_PERIODIC,) * 4)
+    lat = lbmice.Lattice(w.nx, w.ny, **w.params())
+    small = np.zeros(10, dtype=np.float32)
+    with pytest.raises(lbmice.LbmiceError) as ei:
+        lat.load(lbmice.POPS, small)
+    assert ei.value.code == lbmice.EINVAL
+    import ctypes
+    rc = lbmice.lib().lbmice_fields(lat.handle, lbmice.PHI, small.ctypes.data_as(
+        ctypes.c_void_p), small.nbytes, 0)
+    assert rc == lbmice.EINVAL
+    rc = lbmice.lib().lbmice_fields(lat.handle, 42, small.ctypes.data_as(ctypes.c_void_p),
+                                    small.nbytes, 0)
+    assert rc == lbmice.EINVAL
