@@ -32,7 +32,7 @@ from paper_2101_07163_gb300 import workloads as W  # noqa: E402
 
 METRIC = "coupled-lattice MLUPS and % of HBM roofline at 1 GB300 vs FP64 CPU oracle error"
 ALGO_BYTES_PER_LUP = {3: 224, 2: 152}  # read + write of every population and of phi history
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
 
 
 def parse():
@@ -147,15 +147,23 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic(nodes: int):
-    """DRAM bytes per launch from the committed ncu capture, if the kernel is unchanged."""
+    """DRAM bytes per launch from the committed ncu summary ("key = value" lines), scaled
+    to this grid by the node count; None once the kernel source has changed since."""
+    rec = {}
     try:
         with open(PROFILE_TRAFFIC) as fh:
-            rec = json.load(fh)
-    except (OSError, ValueError):
+            for line in fh:
+                line = line.split("#", 1)[0].strip()
+                if "=" in line:
+                    k, v = (t.strip() for t in line.split("=", 1))
+                    rec[k] = v
+    except OSError:
+        return None, None
+    if "dram_bytes_per_node" not in rec:
         return None, None
     if rec.get("kernel_source_sha256_16") != kernel_source_hash():
         return None, rec
-    return rec["dram_bytes_per_node"] * nodes, rec
+    return float(rec["dram_bytes_per_node"]) * nodes, rec
 
 
 def measured_peak():
@@ -314,7 +322,7 @@ def run_ours(args):
 
     # ---- CPU baseline and error against the FP64 oracle, rank 0, N = 1 only ----
     if world == 1 and not args.no_cpu_baseline:
-        fields = W.perturbed_fields(w, 2101, amp_phi=0.05, amp_u=0.01)
+        fields = W.seed_fields(w)
         o, n, dt = oracle_run(w, fields, args.cpu_seconds)
         lat.set_fields(**fields)
         lat.step(n)
@@ -325,7 +333,7 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": nodes * n / dt / 1e6, "unit": "MLUPS", "cores": 1,
                                 "kind": "oracle",
                                 "sample": f"{n} full-grid FP64 oracle steps of {w.name} "
-                                          f"(perturbed seed), single thread"}
+                                          f"from its seed state, single thread"}
         line["oracle_error"] = err
     print(json.dumps(line), flush=True)
     lat.close()
