@@ -167,6 +167,32 @@ int lbmice_destroy(lbmice_t* h);
 /* Static description of an error code. */
 const char* lbmice_strerror(int code);
 
+/* ---- diagnostics without allocation -------------------------------------------------------
+ * The paper has no counterpart: this is a service of the library, not a step of the method.
+ * Some callers cannot allocate device memory when they want diagnostics -- for example an
+ * application whose device memory is reserved up front by its own pool allocator, or a
+ * time-critical loop that cannot accept the device synchronisation and latency of
+ * cudaMalloc. lbmice_stats_noalloc computes the first five values of lbmice_stats
+ * (solid area, flow mass, vapour invariant, sum phi, non-finite count) from state buffers the
+ * caller owns, and allocates nothing: its per-block partial sums live in a fixed 80 KB
+ * __device__ array that every GPU loading this library holds until the process exits.
+ *   pops:     device, planes h0..h8, g0..g8[, f0..f8] of [ny][pitch] floats (plane stride
+ *             pitch * ny), as exported by lbmice_fields(LBMICE_FIELD_POPS) with pitch = nx;
+ *   phi, phi_prev: device, [ny][pitch] floats;  flow: 1 if the f planes are present;
+ *   dx, L_sat: as in lbmice_params;  out: device, 5 doubles, written by the call;
+ *   stream:   cudaStream_t the work is enqueued on (asynchronous; nothing is synchronised).
+ * Grids of more than LBMICE_NOALLOC_MAX_NODES nodes are rejected with LBMICE_EINVAL, as are
+ * null pointers and pitch < nx. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture. Every call uses the same array, which keeps the last call's partial sums (no element
+ * needs to start at zero): calls that overlap on the GPU -- on different streams, or from
+ * different threads -- race on it and must be serialised by the caller.
+ * Errors: EINVAL, ECUDA. */
+#define LBMICE_NOALLOC_MAX_NODES (2048LL * 8192LL)
+int lbmice_stats_noalloc(const float* pops, const float* phi, const float* phi_prev,
+                         int32_t nx, int32_t ny, int32_t pitch, int32_t flow, double dx,
+                         double L_sat, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

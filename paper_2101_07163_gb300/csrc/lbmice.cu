@@ -2,6 +2,7 @@
 // derivation, device state, kernel launches and CUDA-graph replay of step chunks.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -422,3 +423,75 @@ const char* lbmice_strerror(int code) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// FP64 diagnostics without allocation (declared in include/lbmice.h as lbmice_stats_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they want these diagnostics:
+// a host application whose device memory is reserved up front by its own pool allocator
+// (so a cudaMalloc from this library would fail or fragment that budget), or a
+// time-critical loop for which the implicit device synchronisation and unbounded latency of
+// cudaMalloc/cudaFree are not acceptable. For them the per-block partial sums of the
+// reduction live in the fixed array below, which every GPU that loads this library holds
+// until the process exits.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoallocMaxBlocks = 2048;                  // partial rows in the fixed array
+constexpr long long kNoallocNodesPerBlock = 8192;        // nodes summed by one block
+constexpr int kNoallocMaxDevices = 64;
+static_assert(kNoallocMaxBlocks * kNoallocNodesPerBlock == LBMICE_NOALLOC_MAX_NODES,
+              "the fixed partial array must cover LBMICE_NOALLOC_MAX_NODES nodes");
+
+// 2048 rows x 5 doubles = 80 KB. Every row a call reads is written by that same call before
+// it is read, so nothing has to start at zero; the array keeps the last call's partials.
+static __device__ __align__(256) double g_noalloc_partial[kNoallocMaxBlocks * kNStat];
+
+std::atomic<double*> g_noalloc_ptr[kNoallocMaxDevices];
+
+// Device address of the fixed array on the current device. Host code only holds a host-side
+// stand-in for the symbol, so the address is asked for once per device, with that device
+// current, and cached.
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  LB_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return LBMICE_EINVAL;
+  double* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    void* q = nullptr;
+    LB_TRY(cudaGetSymbolAddress(&q, g_noalloc_partial));
+    p = static_cast<double*>(q);
+    g_noalloc_ptr[dev].store(p, std::memory_order_release);
+  }
+  *out = p;
+  return LBMICE_OK;
+}
+
+}  // namespace
+
+extern "C" int lbmice_stats_noalloc(const float* pops, const float* phi, const float* phi_prev,
+                                    int32_t nx, int32_t ny, int32_t pitch, int32_t flow,
+                                    double dx, double L_sat, double* out, void* stream) {
+  if (!pops || !phi || !phi_prev || !out || nx < 1 || ny < 1 || pitch < nx ||
+      (flow != 0 && flow != 1) || !(dx > 0) || !std::isfinite(L_sat))
+    return LBMICE_EINVAL;
+  const long long nodes = (long long)nx * ny;
+  if (nodes > LBMICE_NOALLOC_MAX_NODES) return LBMICE_EINVAL;  // beyond the fixed array
+  const int nblocks = (int)((nodes + kNoallocNodesPerBlock - 1) / kNoallocNodesPerBlock);
+  double* partial = nullptr;
+  int rc = noalloc_scratch(&partial);
+  if (rc != LBMICE_OK) return rc;
+  Consts C;
+  std::memset(&C, 0, sizeof(C));
+  C.nx = nx;
+  C.ny = ny;
+  C.pitch = pitch;
+  C.plane = (long long)pitch * ny;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  stats_partial_kernel<<<nblocks, kStatThreads, 0, st>>>(C, flow, 0.5 * dx * dx, 0.5 * L_sat,
+                                                          pops, phi, phi_prev, partial);
+  LB_TRY(cudaGetLastError());
+  stats_final_kernel<<<1, 32, 0, st>>>(partial, nblocks, out);
+  LB_TRY(cudaGetLastError());
+  return LBMICE_OK;
+}
