@@ -87,7 +87,8 @@ void derive(lbmice_t* h) {
   C.nx = p.nx;
   C.ny = p.ny;
   C.pitch = (p.nx + 31) / 32 * 32;
-  C.plane = (long long)C.pitch * p.ny;
+  C.pstride = (long long)C.pitch * p.ny;  // plane-major: [plane][ny][pitch]
+  C.rstride = C.pitch;
   for (int f = 0; f < 4; ++f) C.bc[f] = p.bc[f];
   const double Dphi = (p.W0 * p.W0 / p.tau0) * p.dt / (p.dx * p.dx);
   h->Dphi3 = 3.0 * Dphi;
@@ -124,7 +125,11 @@ void release(lbmice_t* h) {
   delete h;
 }
 
-size_t pop_bytes(const lbmice_t* h) { return sizeof(float) * h->nplanes * (size_t)h->C.plane; }
+// bytes of one population buffer: nplanes planes of ny rows of pitch floats, whatever the
+// interleaving of planes and rows
+size_t pop_bytes(const lbmice_t* h) {
+  return sizeof(float) * (size_t)h->nplanes * (size_t)h->C.pitch * (size_t)h->C.ny;
+}
 
 int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
   StepPtrs P;
@@ -133,8 +138,7 @@ int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
   P.phi_n = h->phi[s % 3];
   P.phi_nm1 = h->phi[(s + 2) % 3];
   P.phi_np1 = h->phi[(s + 1) % 3];
-  const dim3 blk(kTX, kTY);
-  const dim3 grd = node_grid(h->C, blk);
+  const dim3 grd((h->C.nx + kTX - 1) / kTX, (h->C.ny + kTY - 1) / kTY), blk(kTX, kTY);
   if (h->p.flow)
     step_kernel<kTX, kTY, true>
         <<<grd, blk, Tile<kTX, kTY>::smem_bytes<true>(), st>>>(h->C, P);
@@ -228,8 +232,16 @@ int lbmice_create(const lbmice_params* p, void* stream, lbmice_t** out) {
   h->stream = static_cast<cudaStream_t>(stream);
   h->nplanes = p->flow ? 27 : 18;
   cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_kernel<kTX, kTY, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tile<kTX, kTY>::smem_bytes<true>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_kernel<kTX, kTY, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tile<kTX, kTY>::smem_bytes<false>());
   const size_t field_bytes = sizeof(float) * (size_t)p->nx * p->ny;
-  const size_t phi_bytes = sizeof(float) * (size_t)h->C.plane;
+  const size_t phi_bytes = sizeof(float) * (size_t)h->C.pitch * p->ny;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&h->pops[i], pop_bytes(h));
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&h->phi[i], phi_bytes);
@@ -339,11 +351,13 @@ int lbmice_fields(lbmice_t* h, int32_t which, void* dst, size_t bytes, int32_t d
   if (which == LBMICE_FIELD_POPS) {
     const size_t need = sizeof(float) * h->nplanes * nx * ny;
     if (bytes < need) return LBMICE_EINVAL;
-    LB_TRY(cudaMemcpy2DAsync(dst, nx * sizeof(float), h->pops[s & 1],
-                             h->C.pitch * sizeof(float), nx * sizeof(float),
-                             (size_t)h->nplanes * ny,
-                             dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                             h->stream));
+    for (int q = 0; q < h->nplanes; ++q)
+      LB_TRY(cudaMemcpy2DAsync(static_cast<float*>(dst) + (size_t)q * nx * ny,
+                               nx * sizeof(float), h->pops[s & 1] + q * h->C.pstride,
+                               h->C.rstride * sizeof(float), nx * sizeof(float), ny,
+                               dst_on_device ? cudaMemcpyDeviceToDevice
+                                             : cudaMemcpyDeviceToHost,
+                               h->stream));
   } else {
     const size_t need = sizeof(float) * nx * ny;
     if (bytes < need) return LBMICE_EINVAL;
@@ -368,9 +382,10 @@ int lbmice_load(lbmice_t* h, int32_t which, const void* src, size_t bytes,
   const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (which == LBMICE_FIELD_POPS) {
     if (bytes < sizeof(float) * h->nplanes * nx * ny) return LBMICE_EINVAL;
-    LB_TRY(cudaMemcpy2DAsync(h->pops[s & 1], h->C.pitch * sizeof(float), src,
-                             nx * sizeof(float), nx * sizeof(float), (size_t)h->nplanes * ny,
-                             kind, h->stream));
+    for (int q = 0; q < h->nplanes; ++q)
+      LB_TRY(cudaMemcpy2DAsync(h->pops[s & 1] + q * h->C.pstride, h->C.rstride * sizeof(float),
+                               static_cast<const float*>(src) + (size_t)q * nx * ny,
+                               nx * sizeof(float), nx * sizeof(float), ny, kind, h->stream));
     const dim3 blk(32, 8);
     phi_from_pops_kernel<<<node_grid(h->C, blk), blk, 0, h->stream>>>(h->C, h->pops[s & 1],
                                                                       h->phi[s % 3]);
@@ -486,7 +501,8 @@ extern "C" int lbmice_stats_noalloc(const float* pops, const float* phi, const f
   C.nx = nx;
   C.ny = ny;
   C.pitch = pitch;
-  C.plane = (long long)pitch * ny;
+  C.pstride = (long long)pitch * ny;  // caller's layout: [plane][ny][pitch]
+  C.rstride = pitch;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   stats_partial_kernel<<<nblocks, kStatThreads, 0, st>>>(C, flow, 0.5 * dx * dx, 0.5 * L_sat,
                                                           pops, phi, phi_prev, partial);

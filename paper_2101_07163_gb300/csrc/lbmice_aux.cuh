@@ -62,16 +62,17 @@ __global__ void equilibrium_kernel(const Consts C, double Dphi3, double eps, dou
   const double uy = uy0 ? uy0[i] : 0.0;
   const double uu = ux * ux + uy * uy;
   const long long o = (long long)Y * C.pitch + X;
+  const long long q0 = (long long)Y * C.rstride + X;
   float hv[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const double w = wd_of(a);
     hv[a] = (float)(w * (ph - Dphi3 * cdot(a, Nx, Ny)));
-    pops[(PLANE_H + a) * C.plane + o] = hv[a];
+    pops[(PLANE_H + a) * C.pstride + q0] = hv[a];
     const double cu = cdot(a, ux, uy);
-    pops[(PLANE_G + a) * C.plane + o] = (float)(w * U * (1.0 + 3.0 * cu));
+    pops[(PLANE_G + a) * C.pstride + q0] = (float)(w * U * (1.0 + 3.0 * cu));
     if (FLOW)
-      pops[(PLANE_F + a) * C.plane + o] =
+      pops[(PLANE_F + a) * C.pstride + q0] =
           (float)(w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
   }
   const float s = sum9(hv);
@@ -86,9 +87,10 @@ __global__ void phi_from_pops_kernel(const Consts C, const float* __restrict__ p
   const int Y = blockIdx.y * blockDim.y + threadIdx.y;
   if (X >= C.nx || Y >= C.ny) return;
   const long long o = (long long)Y * C.pitch + X;
+  const long long q0 = (long long)Y * C.rstride + X;
   float hv[9];
 #pragma unroll
-  for (int a = 0; a < 9; ++a) hv[a] = pops[(PLANE_H + a) * C.plane + o];
+  for (int a = 0; a < 9; ++a) hv[a] = pops[(PLANE_H + a) * C.pstride + q0];
   phi[o] = sum9(hv);
 }
 
@@ -101,6 +103,7 @@ __global__ void moment_kernel(const Consts C, int which, int flow,
   const int Y = blockIdx.y * blockDim.y + threadIdx.y;
   if (X >= C.nx || Y >= C.ny) return;
   const long long o = (long long)Y * C.pitch + X;
+  const long long q0 = (long long)Y * C.rstride + X;
   float r = 0.0f;
   if (which == 0) {
     r = phi[o];
@@ -109,14 +112,14 @@ __global__ void moment_kernel(const Consts C, int which, int flow,
   } else if (which == 1) {
     float v[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_G + a) * C.plane + o];
+    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_G + a) * C.pstride + q0];
     r = sum9(v);
   } else if (!flow) {
     r = which == 2 ? 1.0f : 0.0f;
   } else {
     float v[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_F + a) * C.plane + o];
+    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_F + a) * C.pstride + q0];
     const float rho = sum9(v);
     if (which == 2) {
       r = rho;
@@ -148,15 +151,16 @@ __global__ void __launch_bounds__(kStatThreads)
        i += (long long)gridDim.x * blockDim.x) {
     const int Y = (int)(i / C.nx), X = (int)(i - (long long)Y * C.nx);
     const long long o = (long long)Y * C.pitch + X;
+    const long long q0 = (long long)Y * C.rstride + X;
     const float ph = phi[o];
     float v[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_G + a) * C.plane + o];
+    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_G + a) * C.pstride + q0];
     const float U = sum9(v);
     float rho = 1.0f;
     if (flow) {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_F + a) * C.plane + o];
+      for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_F + a) * C.pstride + q0];
       rho = sum9(v);
     }
     acc[0] += area_w * (1.0 + (double)ph);

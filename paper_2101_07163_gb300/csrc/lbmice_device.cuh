@@ -3,11 +3,13 @@
 // equilibrium initialisation, the moment export and the FP64 reductions.
 //
 // State layout in HBM (one allocation per buffer, row pitch padded to 32 floats = 128 B):
-//   populations: planes [h0..h8 | g0..g8 | f0..f8][ny][pitch] float, two buffers (pull
-//                scheme reads one and writes the other);
+//   populations: planes [h0..h8 | g0..g8 | f0..f8][ny][pitch] float, two buffers (the pull
+//                reads one and writes the other);
 //   phi:         three rotating [ny][pitch] float planes holding phi^{n-1}, phi^n, phi^{n+1}
 //                (phi^n feeds the E4 gradient with a two-node halo, phi^{n-1} the d(phi)/dt
 //                of the vapour source, phi^{n+1} = sum h^{n+1} is written by the step).
+// Population q of node (x, y) is at q * pstride + y * rstride + x; the exported layout
+// [q][ny][nx] uses the same formula with pstride = nx ny, rstride = nx.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -67,9 +69,10 @@ enum : int { PLANE_H = 0, PLANE_G = 9, PLANE_F = 18 };
 
 // Lattice constants of one grid, precomputed on the host (lattice units).
 struct Consts {
-  int nx, ny, pitch;
+  int nx, ny, pitch;  // pitch: floats per row of a phi array
   int bc[4];
-  long long plane;   // floats per population plane: pitch * ny
+  long long pstride;  // floats between population planes of one node
+  long long rstride;  // floats between rows of one population plane
   float Dphi3;       // 3 (W0^2/tau0) dt/dx^2: eta = Dphi3 a_s^2 + 1/2, h^eq flux weight
   float dt_tau0;     // dt/tau0: weight of the phase-field source Q
   float lambda;      // coupling of U into Q

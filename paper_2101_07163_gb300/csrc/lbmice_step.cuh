@@ -80,7 +80,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     }
   }
   const long long idx = (long long)my * C.pitch + mx;
-  const float* __restrict__ pin = P.pin + idx;
+  const float* __restrict__ pin = P.pin + (long long)my * C.rstride + mx;
 
   if (inlet >= 0) {
     // Inlet ghost: vapour at the inlet state, flow equilibrium at the adjacent density.
@@ -92,7 +92,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     if (FLOW) {
       float fv[9];
 #pragma unroll
-      for (int a = 0; a < 9; ++a) fv[a] = __ldg(pin + (PLANE_F + a) * C.plane);
+      for (int a = 0; a < 9; ++a) fv[a] = __ldg(pin + (PLANE_F + a) * C.pstride);
       rho = sum9(fv);
     }
     const float uu = ux * ux + uy * uy;
@@ -113,9 +113,9 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   float hv[9], gv[9], fv[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    hv[a] = __ldg(pin + (PLANE_H + a) * C.plane);
-    gv[a] = __ldg(pin + (PLANE_G + a) * C.plane);
-    if (FLOW) fv[a] = __ldg(pin + (PLANE_F + a) * C.plane);
+    hv[a] = __ldg(pin + (PLANE_H + a) * C.pstride);
+    gv[a] = __ldg(pin + (PLANE_G + a) * C.pstride);
+    if (FLOW) fv[a] = __ldg(pin + (PLANE_F + a) * C.pstride);
   }
   const float php = __ldg(P.phi_nm1 + idx);
   const int pc = (ly + 1) * T::PW + (lx + 1);
@@ -135,11 +135,25 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   const float pSE = sphi[pc - T::PW + 1], pSW = sphi[pc - T::PW - 1];
   const float gx = kW1 * (pE - pW) + kW2 * ((pNE - pNW) + (pSE - pSW));
   const float gy = kW1 * (pN - pS) + kW2 * ((pNE - pSE) + (pNW - pSW));
-  float as, Nx, Ny;
-  aniso(gx, gy, C.eps, C.kN6eps, as, Nx, Ny);
+  float as = 1.0f, Nx = 0.0f, Ny = 0.0f;
+  {
+    const float s2 = gx * gx + gy * gy;
+    if (s2 > 1e-12f) {  // |grad phi|^2 <= 1e-12: isotropic, no anisotropic flux
+      const float rinv = rsqrtf(s2);
+      const float nx = gx * rinv, ny = gy * rinv;
+      const float X2 = nx * nx, Y2 = ny * ny;
+      const float cos6 =
+          X2 * X2 * X2 - 15.0f * X2 * X2 * Y2 + 15.0f * X2 * Y2 * Y2 - Y2 * Y2 * Y2;
+      const float sin6 = nx * ny * (6.0f * X2 * X2 - 20.0f * X2 * Y2 + 6.0f * Y2 * Y2);
+      as = 1.0f + C.eps * cos6;
+      const float t = C.kN6eps * as * sin6;
+      Nx = t * gy;
+      Ny = -(t * gx);
+    }
+  }
   const float as2 = as * as;
-  const float inv_as2 = 1.0f / as2;
-  const float inv_eta = 1.0f / (C.Dphi3 * as2 + 0.5f);
+  const float inv_as2 = __fdividef(1.0f, as2);
+  const float inv_eta = __fdividef(1.0f, C.Dphi3 * as2 + 0.5f);
   const float omp2 = 1.0f - ph * ph;
   const float srcQ = (ph - ph * ph * ph + C.lambda * U * omp2 * omp2) * C.dt_tau0;
 
@@ -148,14 +162,14 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   if (FLOW) {
     const float onep = 1.0f + ph;
     k = C.kdrag * rho * onep * onep * (1.0f - ph);
-    const float inv = 1.0f / (rho + 0.5f * k);
+    const float inv = __fdividef(1.0f, rho + 0.5f * k);
     const float sfac = 0.5f * (1.0f - ph);
     usx = sfac * (jx * inv);
     usy = sfac * (jy * inv);
   }
   // ---- vapour relaxation and source (Sec. 2.2.2) ----
   const float q = fminf(fmaxf(1.0f - ph, 0.0f), 2.0f);
-  const float inv_tg = 1.0f / (C.Dlat3 * q + 0.5f);
+  const float inv_tg = __fdividef(1.0f, C.Dlat3 * q + 0.5f);
   const float srcU = -C.half_Lsat * (ph - php);
 
   if (OWN) {
@@ -239,14 +253,15 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const Step
   const int X = x0 + tx, Y = y0 + ty;
   if (X >= C.nx || Y >= C.ny) return;
   const long long idx = (long long)Y * C.pitch + X;
+  float* __restrict__ out = P.pout + (long long)Y * C.rstride + X;
   float hn[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const int src = (ty + 1 - cy_of(a)) * T::SW + (tx + 1 - cx_of(a));
     hn[a] = fmaf(hown[a], sB[src], spost[(PLANE_H + a) * T::SN + src]);
-    P.pout[(PLANE_H + a) * C.plane + idx] = hn[a];
-    P.pout[(PLANE_G + a) * C.plane + idx] = spost[(PLANE_G + a) * T::SN + src];
-    if (FLOW) P.pout[(PLANE_F + a) * C.plane + idx] = spost[(PLANE_F + a) * T::SN + src];
+    out[(PLANE_H + a) * C.pstride] = hn[a];
+    out[(PLANE_G + a) * C.pstride] = spost[(PLANE_G + a) * T::SN + src];
+    if (FLOW) out[(PLANE_F + a) * C.pstride] = spost[(PLANE_F + a) * T::SN + src];
   }
   P.phi_np1[idx] = sum9(hn);
 }
