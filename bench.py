@@ -31,7 +31,12 @@ sys.path.insert(0, ROOT)
 from paper_2101_07163_gb300 import workloads as W  # noqa: E402
 
 METRIC = "coupled-lattice MLUPS and % of HBM roofline at 1 GB300 vs FP64 CPU oracle error"
-ALGO_BYTES_PER_LUP = {3: 224, 2: 152}  # read + write of every population and of phi history
+# read + write of every population and of the phi history, per node update (all lattices)
+ALGO_BYTES_PER_LUP = {("f32", 3): 224, ("f32", 2): 152, ("f16", 3): 116, ("f16", 2): 80,
+                      ("bf16", 3): 116, ("bf16", 2): 80}
+# what this design moves: + phi^n read; 16-bit storage adds the FP32 moments U (and rho)
+DESIGN_BYTES_PER_LUP = {("f32", 3): 228, ("f32", 2): 156, ("f16", 3): 124, ("f16", 2): 84,
+                        ("bf16", 3): 124, ("bf16", 2): 84}
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
 
 
@@ -46,6 +51,8 @@ def parse():
     ap.add_argument("--ny", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--storage-legs", default="f16,bf16",
+                    help="16-bit storage legs timed after the FP32 leg ('' for none)")
     return ap.parse_args()
 
 
@@ -279,14 +286,32 @@ def run_ours(args):
     lat2.close()
     del lat2
 
+    # ---- 16-bit storage legs: same workload, same timed region ----
+    legs = {}
+    for st in [x for x in args.storage_legs.split(",") if x]:
+        lat3 = lbmice.Lattice(w.nx, w.ny, stream=stream, storage=st, **w.params())
+        lat3.init_seed(w.cx, w.cy, w.R0, w.U0)
+        lat3.step(args.warmup)
+        lat3.sync()
+        barrier(dist)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat3.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms3 = max_over_ranks(dist, e0.elapsed_time(e1))
+        legs[st] = {"lat": lat3, "ms": ms3}
+
     if rank != 0:
+        for leg in legs.values():
+            leg["lat"].close()
         lat.close()
         barrier(dist)
         return
 
     value = nodes * args.steps * world / (ms * 1e-3) / 1e6
     per_launch_ms = ms / args.steps
-    algo = ALGO_BYTES_PER_LUP[w.lattices] * nodes
+    algo = ALGO_BYTES_PER_LUP[("f32", w.lattices)] * nodes
     achieved = algo / (per_launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
     traffic, rec = profiled_traffic(nodes)
@@ -294,8 +319,9 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs copy bandwidth)"
                 if peak_kind == "measured" else peak_kind,
-                "algorithmic_bytes_per_lup": ALGO_BYTES_PER_LUP[w.lattices],
-                "kernel": "lbmice::step_kernel"}
+                "algorithmic_bytes_per_lup": ALGO_BYTES_PER_LUP[("f32", w.lattices)],
+                "design_bytes_per_lup": DESIGN_BYTES_PER_LUP[("f32", w.lattices)],
+                "kernel": "lbmice::step_kernel<32,8,flow,F32>"}
     if rec is not None:
         roofline["traffic_source"] = rec.get("source")
         if traffic is None:
@@ -319,6 +345,21 @@ def run_ours(args):
                 "note": "set_fields from pinned host + K steps + stats + phi to host"},
         "finite": bool(finite and st2["nonfinite"] == 0),
     }
+    if legs:
+        out = {}
+        for st, leg in legs.items():
+            ms3 = leg["ms"]
+            algo3 = ALGO_BYTES_PER_LUP[(st, w.lattices)] * nodes
+            ach3 = algo3 / (ms3 / args.steps * 1e-3) / 1e9
+            out[st] = {"value": nodes * args.steps * world / (ms3 * 1e-3) / 1e6,
+                       "unit": "MLUPS", "ms_per_step": ms3 / args.steps,
+                       "roofline": {"bound": "hbm", "achieved": ach3, "peak": peak,
+                                    "unit": "GB/s", "frac": ach3 / peak,
+                                    "algorithmic_bytes_per_lup":
+                                        ALGO_BYTES_PER_LUP[(st, w.lattices)],
+                                    "design_bytes_per_lup":
+                                        DESIGN_BYTES_PER_LUP[(st, w.lattices)]}}
+        line["storage_legs"] = out
 
     # ---- CPU baseline and error against the FP64 oracle, rank 0, N = 1 only ----
     if world == 1 and not args.no_cpu_baseline:
@@ -335,8 +376,19 @@ def run_ours(args):
                                 "sample": f"{n} full-grid FP64 oracle steps of {w.name} "
                                           f"from its seed state, single thread"}
         line["oracle_error"] = err
+        ophi, oU = o.field(0), o.field(1)
+        for st, leg in legs.items():
+            l3 = leg["lat"]
+            l3.set_fields(**fields)
+            l3.step(n)
+            line["storage_legs"][st]["oracle_error"] = {
+                "steps": n,
+                "max_dphi": float(np.abs(l3.field(lbmice.PHI) - ophi).max()),
+                "max_dU": float(np.abs(l3.field(lbmice.U) - oU).max())}
     print(json.dumps(line), flush=True)
     lat.close()
+    for leg in legs.values():
+        leg["lat"].close()
     barrier(dist)
 
 

@@ -70,8 +70,21 @@ extern "C" {
 #define LBMICE_FIELD_UX 3       /* u*_x = (1-phi)/2 j_x/(rho + k/2)           float[ny][nx] */
 #define LBMICE_FIELD_UY 4       /* u*_y                                       float[ny][nx] */
 #define LBMICE_FIELD_PHI_PREV 5 /* phi one step earlier (d(phi)/dt history)   float[ny][nx] */
-#define LBMICE_FIELD_POPS 6     /* raw populations, planes h0..h8, g0..g8 and, with flow,
-                                   f0..f8: float[18 or 27][ny][nx]                        */
+#define LBMICE_FIELD_POPS 6     /* populations, planes h0..h8, g0..g8 and, with flow,
+                                   f0..f8: float[18 or 27][ny][nx] (decoded to float for
+                                   16-bit storage)                                         */
+#define LBMICE_FIELD_STATE 7    /* the whole state in its storage format, opaque bytes
+                                   (lbmice_state_bytes); loading it restores a run exactly */
+
+/* ---- storage of the populations (spec precision form; arithmetic is FP32) --------
+ * F32:  every population as float (224 B moved per node update with all three lattices).
+ * F16, BF16: per lattice the zeroth moment (phi, U, rho) as float and the 8 moving
+ *       populations as 16-bit deviations p_a - w_a M from the local rest state; the rest
+ *       population is rebuilt as w_0 M - sum of deviations, so the moments are stored
+ *       exactly (124 B moved per node update with all three lattices).                   */
+#define LBMICE_STORAGE_F32 0
+#define LBMICE_STORAGE_F16 1
+#define LBMICE_STORAGE_BF16 2
 
 #define LBMICE_NSTATS 6
 
@@ -92,6 +105,7 @@ typedef struct lbmice_params {
   int32_t bc[4];        /* faces -x, +x, -y, +y: LBMICE_BC_*                               */
   int32_t flow;         /* 1: evolve the flow lattice f; 0: fluid at rest, f not stored    */
   int32_t check_every;  /* lbmice_step checks for NaN/Inf every this many steps (0: never) */
+  int32_t storage;      /* LBMICE_STORAGE_* (default F32)                                  */
 } lbmice_params;
 
 typedef struct lbmice_ctx lbmice_t;
@@ -132,14 +146,17 @@ int lbmice_set_fields(lbmice_t* h, const double* phi, const double* U, const dou
 int lbmice_step(lbmice_t* h, int64_t nsteps);
 
 /* Copy one field (LBMICE_FIELD_*) of the current state into dst, which holds bytes bytes
- * (must be at least the field's size: 4 nx ny, or 4 nx ny times 18 or 27 for POPS).
+ * (must be at least the field's size: 4 nx ny, 4 nx ny times 18 or 27 for POPS,
+ * lbmice_state_bytes for STATE).
  * dst_on_device: 1 = device pointer (asynchronous), 0 = host pointer (the call
  * synchronises the stream before returning). Errors: EINVAL, ECUDA. */
 int lbmice_fields(lbmice_t* h, int32_t which, void* dst, size_t bytes, int32_t dst_on_device);
 
 /* Overwrite the state from a checkpoint: which = LBMICE_FIELD_POPS (layout as in
- * lbmice_fields; phi is recomputed as sum h) or LBMICE_FIELD_PHI_PREV. src holds bytes
- * bytes, on the device (1) or host (0). Loading both restores a state exactly.
+ * lbmice_fields; phi, and with 16-bit storage U and rho, are recomputed as the sums),
+ * LBMICE_FIELD_PHI_PREV, or LBMICE_FIELD_STATE (bytes from lbmice_fields(STATE) of a handle
+ * with the same parameters). src holds bytes bytes, on the device (1) or host (0). Loading
+ * POPS and PHI_PREV restores an F32 state exactly; STATE restores any storage exactly.
  * Errors: EINVAL, ECUDA. */
 int lbmice_load(lbmice_t* h, int32_t which, const void* src, size_t bytes,
                 int32_t src_on_device);
@@ -153,6 +170,9 @@ int lbmice_load(lbmice_t* h, int32_t which, const void* src, size_t bytes,
  *   out[5] time steps taken since the last init
  * Synchronises the stream. Errors: EINVAL, ECUDA. */
 int lbmice_stats(lbmice_t* h, double out[LBMICE_NSTATS]);
+
+/* Size in bytes of the LBMICE_FIELD_STATE blob of this handle (0 for a null handle). */
+size_t lbmice_state_bytes(const lbmice_t* h);
 
 /* Wait for the handle's stream and report any pending asynchronous CUDA error. */
 int lbmice_sync(lbmice_t* h);

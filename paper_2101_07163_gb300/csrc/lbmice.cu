@@ -34,8 +34,11 @@ struct lbmice_ctx {
   cudaStream_t stream = nullptr;   // caller's stream: every launch goes here
   cudaStream_t capture = nullptr;  // private stream used only to record graphs
   int nplanes = 0;
-  float* pops[2] = {nullptr, nullptr};
+  size_t elem = 4;                 // bytes per stored population
+  void* pops[2] = {nullptr, nullptr};
   float* phi[3] = {nullptr, nullptr, nullptr};
+  float* Um[2] = {nullptr, nullptr};   // 16-bit storage: U (zeroth moment of g), ping-pong
+  float* rhom[2] = {nullptr, nullptr}; // 16-bit storage with flow: rho, ping-pong
   float* fieldbuf = nullptr;       // one contiguous float field, for host exports
   double* stat_partial = nullptr;
   double* stat_out = nullptr;
@@ -75,6 +78,7 @@ int validate(const lbmice_params& p) {
   if ((p.bc[2] == LBMICE_BC_PERIODIC) != (p.bc[3] == LBMICE_BC_PERIODIC)) return LBMICE_EINVAL;
   if (p.flow != 0 && p.flow != 1) return LBMICE_EINVAL;
   if (p.check_every < 0) return LBMICE_EINVAL;
+  if (p.storage < LBMICE_STORAGE_F32 || p.storage > LBMICE_STORAGE_BF16) return LBMICE_EINVAL;
   if (!std::isfinite(p.u_in) || std::fabs(p.u_in) >= std::sqrt(1.0 / 3.0)) return LBMICE_EUNSTABLE;
   if (p.flow && !(p.nu > 0)) return LBMICE_EUNSTABLE;  // tau_f = 3 nu + 1/2 must exceed 1/2
   return LBMICE_OK;
@@ -115,8 +119,10 @@ void derive(lbmice_t* h) {
 
 void release(lbmice_t* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  for (float* b : h->pops) if (b) cudaFree(b);
+  for (void* b : h->pops) if (b) cudaFree(b);
   for (float* b : h->phi) if (b) cudaFree(b);
+  for (float* b : h->Um) if (b) cudaFree(b);
+  for (float* b : h->rhom) if (b) cudaFree(b);
   if (h->fieldbuf) cudaFree(h->fieldbuf);
   if (h->stat_partial) cudaFree(h->stat_partial);
   if (h->stat_out) cudaFree(h->stat_out);
@@ -125,10 +131,24 @@ void release(lbmice_t* h) {
   delete h;
 }
 
-// bytes of one population buffer: nplanes planes of ny rows of pitch floats, whatever the
+// bytes of one population buffer: nplanes planes of ny rows of pitch values, whatever the
 // interleaving of planes and rows
 size_t pop_bytes(const lbmice_t* h) {
-  return sizeof(float) * (size_t)h->nplanes * (size_t)h->C.pitch * (size_t)h->C.ny;
+  return h->elem * (size_t)h->nplanes * (size_t)h->C.pitch * (size_t)h->C.ny;
+}
+size_t field_bytes(const lbmice_t* h) {
+  return sizeof(float) * (size_t)h->C.pitch * (size_t)h->C.ny;
+}
+bool dev16(const lbmice_t* h) { return h->p.storage != LBMICE_STORAGE_F32; }
+
+// Run f with a tag value of the handle's storage type.
+template <class Fn>
+int with_storage(const lbmice_t* h, Fn&& fn) {
+  switch (h->p.storage) {
+    case LBMICE_STORAGE_F16: return fn(F16{});
+    case LBMICE_STORAGE_BF16: return fn(BF16{});
+    default: return fn(F32{});
+  }
 }
 
 int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
@@ -138,14 +158,21 @@ int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
   P.phi_n = h->phi[s % 3];
   P.phi_nm1 = h->phi[(s + 2) % 3];
   P.phi_np1 = h->phi[(s + 1) % 3];
+  P.U_n = h->Um[s & 1];
+  P.U_np1 = h->Um[(s + 1) & 1];
+  P.rho_n = h->rhom[s & 1];
+  P.rho_np1 = h->rhom[(s + 1) & 1];
   const dim3 grd((h->C.nx + kTX - 1) / kTX, (h->C.ny + kTY - 1) / kTY), blk(kTX, kTY);
-  if (h->p.flow)
-    step_kernel<kTX, kTY, true>
-        <<<grd, blk, Tile<kTX, kTY>::smem_bytes<true>(), st>>>(h->C, P);
-  else
-    step_kernel<kTX, kTY, false>
-        <<<grd, blk, Tile<kTX, kTY>::smem_bytes<false>(), st>>>(h->C, P);
-  return cuda_err(cudaGetLastError());
+  return with_storage(h, [&](auto tag) {
+    using S = decltype(tag);
+    if (h->p.flow)
+      step_kernel<kTX, kTY, true, S>
+          <<<grd, blk, Tile<kTX, kTY>::smem_bytes<true>(), st>>>(h->C, P);
+    else
+      step_kernel<kTX, kTY, false, S>
+          <<<grd, blk, Tile<kTX, kTY>::smem_bytes<false>(), st>>>(h->C, P);
+    return cuda_err(cudaGetLastError());
+  });
 }
 
 int ensure_graph(lbmice_t* h) {
@@ -165,10 +192,14 @@ int ensure_graph(lbmice_t* h) {
 
 int run_stats(lbmice_t* h) {
   const int64_t s = h->step;
-  stats_partial_kernel<<<kStatBlocks, kStatThreads, 0, h->stream>>>(
-      h->C, h->p.flow, 0.5 * h->p.dx * h->p.dx, 0.5 * h->p.L_sat, h->pops[s & 1],
-      h->phi[s % 3], h->phi[(s + 2) % 3], h->stat_partial);
-  LB_TRY(cudaGetLastError());
+  int rc = with_storage(h, [&](auto tag) {
+    using S = decltype(tag);
+    stats_partial_kernel<S><<<kStatBlocks, kStatThreads, 0, h->stream>>>(
+        h->C, h->p.flow, 0.5 * h->p.dx * h->p.dx, 0.5 * h->p.L_sat, h->pops[s & 1],
+        h->phi[s % 3], h->phi[(s + 2) % 3], h->Um[s & 1], h->rhom[s & 1], h->stat_partial);
+    return cuda_err(cudaGetLastError());
+  });
+  if (rc != LBMICE_OK) return rc;
   stats_final_kernel<<<1, 32, 0, h->stream>>>(h->stat_partial, kStatBlocks, h->stat_out);
   LB_TRY(cudaGetLastError());
   LB_TRY(cudaMemcpyAsync(h->stat_host, h->stat_out, kNStat * sizeof(double),
@@ -183,15 +214,19 @@ int equilibrium_from(lbmice_t* h, const double* phi, const double* U, const doub
   const dim3 blk(32, 8);
   const dim3 grd = node_grid(h->C, blk);
   const double eps = h->p.eps, kN6eps = h->p.kappa_N * 6.0 * h->p.eps;
-  if (h->p.flow)
-    equilibrium_kernel<true><<<grd, blk, 0, h->stream>>>(h->C, h->Dphi3, eps, kN6eps, phi, U,
-                                                         rho, ux, uy, h->pops[0], h->phi[0],
-                                                         h->phi[2]);
-  else
-    equilibrium_kernel<false><<<grd, blk, 0, h->stream>>>(h->C, h->Dphi3, eps, kN6eps, phi,
-                                                          U, rho, ux, uy, h->pops[0],
-                                                          h->phi[0], h->phi[2]);
-  LB_TRY(cudaGetLastError());
+  int rc = with_storage(h, [&](auto tag) {
+    using S = decltype(tag);
+    if (h->p.flow)
+      equilibrium_kernel<true, S><<<grd, blk, 0, h->stream>>>(
+          h->C, h->Dphi3, eps, kN6eps, phi, U, rho, ux, uy, h->pops[0], h->phi[0], h->phi[2],
+          h->Um[0], h->rhom[0]);
+    else
+      equilibrium_kernel<false, S><<<grd, blk, 0, h->stream>>>(
+          h->C, h->Dphi3, eps, kN6eps, phi, U, rho, ux, uy, h->pops[0], h->phi[0], h->phi[2],
+          h->Um[0], h->rhom[0]);
+    return cuda_err(cudaGetLastError());
+  });
+  if (rc != LBMICE_OK) return rc;
   h->step = 0;
   return LBMICE_OK;
 }
@@ -231,21 +266,19 @@ int lbmice_create(const lbmice_params* p, void* stream, lbmice_t** out) {
   derive(h);
   h->stream = static_cast<cudaStream_t>(stream);
   h->nplanes = p->flow ? 27 : 18;
+  h->elem = p->storage == LBMICE_STORAGE_F32 ? 4 : 2;
   cudaError_t e = cudaGetDevice(&h->device);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_kernel<kTX, kTY, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Tile<kTX, kTY>::smem_bytes<true>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_kernel<kTX, kTY, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Tile<kTX, kTY>::smem_bytes<false>());
-  const size_t field_bytes = sizeof(float) * (size_t)p->nx * p->ny;
-  const size_t phi_bytes = sizeof(float) * (size_t)h->C.pitch * p->ny;
+  const size_t out_bytes = sizeof(float) * (size_t)p->nx * p->ny;
+  const size_t phi_bytes = field_bytes(h);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&h->pops[i], pop_bytes(h));
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&h->phi[i], phi_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&h->fieldbuf, field_bytes);
+  if (dev16(h)) {
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&h->Um[i], phi_bytes);
+    for (int i = 0; i < 2 && e == cudaSuccess && p->flow; ++i)
+      e = cudaMalloc(&h->rhom[i], phi_bytes);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&h->fieldbuf, out_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->stat_partial, sizeof(double) * kStatBlocks * kNStat);
   if (e == cudaSuccess) e = cudaMalloc(&h->stat_out, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMallocHost(&h->stat_host, sizeof(double) * 8);
@@ -253,6 +286,10 @@ int lbmice_create(const lbmice_params* p, void* stream, lbmice_t** out) {
     e = cudaMemsetAsync(h->pops[i], 0, pop_bytes(h), h->stream);
   for (int i = 0; i < 3 && e == cudaSuccess; ++i)
     e = cudaMemsetAsync(h->phi[i], 0, phi_bytes, h->stream);
+  for (float* b : h->Um)
+    if (b && e == cudaSuccess) e = cudaMemsetAsync(b, 0, phi_bytes, h->stream);
+  for (float* b : h->rhom)
+    if (b && e == cudaSuccess) e = cudaMemsetAsync(b, 0, phi_bytes, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     release(h);
@@ -267,10 +304,12 @@ int lbmice_init_seed(lbmice_t* h, double cx, double cy, double R0, double U0) {
   if (!h || !std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(R0) ||
       !std::isfinite(U0))
     return LBMICE_EINVAL;
-  // The second population buffer is free before the first step: it holds the five double
-  // seed fields (40 bytes per node; it has 72 or 108).
+  // The second population buffer is free before the first step: it holds the double seed
+  // fields (phi and U, plus rho and u with flow: 16 or 40 bytes per node; it has at least 36
+  // or 54).
   const size_t n = (size_t)h->p.nx * h->p.ny;
   double* f = reinterpret_cast<double*>(h->pops[1]);
+  const bool fl = h->p.flow != 0;
   // velocity of the first inlet face along its inward normal (the fluid rests otherwise)
   double ux = 0.0, uy = 0.0;
   const double nxs[4] = {1, -1, 0, 0}, nys[4] = {0, 0, 1, -1};
@@ -282,11 +321,14 @@ int lbmice_init_seed(lbmice_t* h, double cx, double cy, double R0, double U0) {
     }
   const dim3 blk(32, 8);
   const dim3 grd = node_grid(h->C, blk);
+  double* rho = fl ? f + 2 * n : nullptr;
+  double* uxf = fl ? f + 3 * n : nullptr;
+  double* uyf = fl ? f + 4 * n : nullptr;
   seed_kernel<<<grd, blk, 0, h->stream>>>(h->p.nx, h->p.ny, cx, cy, R0, U0,
                                           std::sqrt(2.0) * h->p.W0 / h->p.dx, ux, uy, f,
-                                          f + n, f + 2 * n, f + 3 * n, f + 4 * n);
+                                          f + n, rho, uxf, uyf);
   LB_TRY(cudaGetLastError());
-  return equilibrium_from(h, f, f + n, f + 2 * n, f + 3 * n, f + 4 * n);
+  return equilibrium_from(h, f, f + n, rho, uxf, uyf);
 }
 
 int lbmice_set_fields(lbmice_t* h, const double* phi, const double* U, const double* rho,
@@ -295,7 +337,8 @@ int lbmice_set_fields(lbmice_t* h, const double* phi, const double* U, const dou
   if (on_device) return equilibrium_from(h, phi, U, rho, ux, uy);
   const size_t n = (size_t)h->p.nx * h->p.ny;
   double* f = reinterpret_cast<double*>(h->pops[1]);
-  const double* src[5] = {phi, U, rho, ux, uy};
+  const bool fl = h->p.flow != 0;  // without flow the velocity inputs are ignored
+  const double* src[5] = {phi, U, fl ? rho : nullptr, fl ? ux : nullptr, fl ? uy : nullptr};
   const double* dev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   for (int k = 0; k < 5; ++k) {
     if (!src[k]) continue;
@@ -342,30 +385,109 @@ int lbmice_step(lbmice_t* h, int64_t nsteps) {
   return LBMICE_OK;
 }
 
-int lbmice_fields(lbmice_t* h, int32_t which, void* dst, size_t bytes, int32_t dst_on_device) {
-  if (!h || !dst || which < 0 || which > LBMICE_FIELD_POPS ||
+}  // extern "C"
+
+namespace {
+
+// The pieces of the exact state, in blob order: populations, phi^n, phi^{n-1}, and with
+// 16-bit storage U and rho of the current slot.
+struct StatePart {
+  void* ptr;
+  size_t bytes;
+};
+int state_parts(lbmice_t* h, StatePart parts[5]) {
+  const int64_t s = h->step;
+  int n = 0;
+  parts[n++] = {h->pops[s & 1], pop_bytes(h)};
+  parts[n++] = {h->phi[s % 3], field_bytes(h)};
+  parts[n++] = {h->phi[(s + 2) % 3], field_bytes(h)};
+  if (h->Um[0]) parts[n++] = {h->Um[s & 1], field_bytes(h)};
+  if (h->rhom[0]) parts[n++] = {h->rhom[s & 1], field_bytes(h)};
+  return n;
+}
+
+}  // namespace
+
+extern "C" size_t lbmice_state_bytes(const lbmice_t* h) {
+  if (!h) return 0;
+  StatePart parts[5];
+  const int n = state_parts(const_cast<lbmice_t*>(h), parts);
+  size_t total = 0;
+  for (int k = 0; k < n; ++k) total += parts[k].bytes;
+  return total;
+}
+
+namespace {
+
+int copy_state(lbmice_t* h, void* blob, bool out, cudaMemcpyKind kind) {
+  StatePart parts[5];
+  const int n = state_parts(h, parts);
+  char* b = static_cast<char*>(blob);
+  for (int k = 0; k < n; ++k) {
+    if (out)
+      LB_TRY(cudaMemcpyAsync(b, parts[k].ptr, parts[k].bytes, kind, h->stream));
+    else
+      LB_TRY(cudaMemcpyAsync(parts[k].ptr, b, parts[k].bytes, kind, h->stream));
+    b += parts[k].bytes;
+  }
+  return LBMICE_OK;
+}
+
+}  // namespace
+
+extern "C" int lbmice_fields(lbmice_t* h, int32_t which, void* dst, size_t bytes,
+                             int32_t dst_on_device) {
+  if (!h || !dst || which < 0 || which > LBMICE_FIELD_STATE ||
       (dst_on_device != 0 && dst_on_device != 1))
     return LBMICE_EINVAL;
   const int64_t s = h->step;
   const size_t nx = h->p.nx, ny = h->p.ny;
-  if (which == LBMICE_FIELD_POPS) {
+  const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const dim3 blk(32, 8);
+  if (which == LBMICE_FIELD_STATE) {
+    if (bytes < lbmice_state_bytes(h)) return LBMICE_EINVAL;
+    int rc = copy_state(h, dst, true, kind);
+    if (rc != LBMICE_OK) return rc;
+  } else if (which == LBMICE_FIELD_POPS) {
     const size_t need = sizeof(float) * h->nplanes * nx * ny;
     if (bytes < need) return LBMICE_EINVAL;
-    for (int q = 0; q < h->nplanes; ++q)
-      LB_TRY(cudaMemcpy2DAsync(static_cast<float*>(dst) + (size_t)q * nx * ny,
-                               nx * sizeof(float), h->pops[s & 1] + q * h->C.pstride,
-                               h->C.rstride * sizeof(float), nx * sizeof(float), ny,
-                               dst_on_device ? cudaMemcpyDeviceToDevice
-                                             : cudaMemcpyDeviceToHost,
-                               h->stream));
+    if (!dev16(h)) {
+      const float* pops = static_cast<const float*>(h->pops[s & 1]);
+      for (int q = 0; q < h->nplanes; ++q)
+        LB_TRY(cudaMemcpy2DAsync(static_cast<float*>(dst) + (size_t)q * nx * ny,
+                                 nx * sizeof(float), pops + q * h->C.pstride,
+                                 h->C.rstride * sizeof(float), nx * sizeof(float), ny, kind,
+                                 h->stream));
+    } else {
+      // decode one plane at a time (into dst directly, or through the field buffer)
+      for (int q = 0; q < h->nplanes; ++q) {
+        float* out = dst_on_device ? static_cast<float*>(dst) + (size_t)q * nx * ny
+                                   : h->fieldbuf;
+        int rc = with_storage(h, [&](auto tag) {
+          using S = decltype(tag);
+          decode_plane_kernel<S><<<node_grid(h->C, blk), blk, 0, h->stream>>>(
+              h->C, h->pops[s & 1], q / 9, q % 9, h->phi[s % 3], h->Um[s & 1], h->rhom[s & 1],
+              out);
+          return cuda_err(cudaGetLastError());
+        });
+        if (rc != LBMICE_OK) return rc;
+        if (!dst_on_device)
+          LB_TRY(cudaMemcpyAsync(static_cast<float*>(dst) + (size_t)q * nx * ny, h->fieldbuf,
+                                 sizeof(float) * nx * ny, cudaMemcpyDeviceToHost, h->stream));
+      }
+    }
   } else {
     const size_t need = sizeof(float) * nx * ny;
     if (bytes < need) return LBMICE_EINVAL;
     float* out = dst_on_device ? static_cast<float*>(dst) : h->fieldbuf;
-    const dim3 blk(32, 8);
-    moment_kernel<<<node_grid(h->C, blk), blk, 0, h->stream>>>(
-        h->C, which, h->p.flow, h->pops[s & 1], h->phi[s % 3], h->phi[(s + 2) % 3], out);
-    LB_TRY(cudaGetLastError());
+    int rc = with_storage(h, [&](auto tag) {
+      using S = decltype(tag);
+      moment_kernel<S><<<node_grid(h->C, blk), blk, 0, h->stream>>>(
+          h->C, which, h->p.flow, h->pops[s & 1], h->phi[s % 3], h->phi[(s + 2) % 3],
+          h->Um[s & 1], h->rhom[s & 1], out);
+      return cuda_err(cudaGetLastError());
+    });
+    if (rc != LBMICE_OK) return rc;
     if (!dst_on_device)
       LB_TRY(cudaMemcpyAsync(dst, h->fieldbuf, need, cudaMemcpyDeviceToHost, h->stream));
   }
@@ -373,23 +495,48 @@ int lbmice_fields(lbmice_t* h, int32_t which, void* dst, size_t bytes, int32_t d
   return LBMICE_OK;
 }
 
-int lbmice_load(lbmice_t* h, int32_t which, const void* src, size_t bytes,
-                int32_t src_on_device) {
+extern "C" int lbmice_load(lbmice_t* h, int32_t which, const void* src, size_t bytes,
+                           int32_t src_on_device) {
   if (!h || !src || (src_on_device != 0 && src_on_device != 1)) return LBMICE_EINVAL;
-  if (which != LBMICE_FIELD_POPS && which != LBMICE_FIELD_PHI_PREV) return LBMICE_EINVAL;
+  if (which != LBMICE_FIELD_POPS && which != LBMICE_FIELD_PHI_PREV &&
+      which != LBMICE_FIELD_STATE)
+    return LBMICE_EINVAL;
   const int64_t s = h->step;
   const size_t nx = h->p.nx, ny = h->p.ny;
   const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (which == LBMICE_FIELD_POPS) {
+  const dim3 blk(32, 8);
+  if (which == LBMICE_FIELD_STATE) {
+    if (bytes < lbmice_state_bytes(h)) return LBMICE_EINVAL;
+    int rc = copy_state(h, const_cast<void*>(src), false, kind);
+    if (rc != LBMICE_OK) return rc;
+  } else if (which == LBMICE_FIELD_POPS) {
     if (bytes < sizeof(float) * h->nplanes * nx * ny) return LBMICE_EINVAL;
-    for (int q = 0; q < h->nplanes; ++q)
-      LB_TRY(cudaMemcpy2DAsync(h->pops[s & 1] + q * h->C.pstride, h->C.rstride * sizeof(float),
-                               static_cast<const float*>(src) + (size_t)q * nx * ny,
-                               nx * sizeof(float), nx * sizeof(float), ny, kind, h->stream));
-    const dim3 blk(32, 8);
-    phi_from_pops_kernel<<<node_grid(h->C, blk), blk, 0, h->stream>>>(h->C, h->pops[s & 1],
-                                                                      h->phi[s % 3]);
-    LB_TRY(cudaGetLastError());
+    if (!dev16(h)) {
+      float* pops = static_cast<float*>(h->pops[s & 1]);
+      for (int q = 0; q < h->nplanes; ++q)
+        LB_TRY(cudaMemcpy2DAsync(pops + q * h->C.pstride, h->C.rstride * sizeof(float),
+                                 static_cast<const float*>(src) + (size_t)q * nx * ny,
+                                 nx * sizeof(float), nx * sizeof(float), ny, kind, h->stream));
+      phi_from_pops_kernel<<<node_grid(h->C, blk), blk, 0, h->stream>>>(h->C, pops,
+                                                                        h->phi[s % 3]);
+      LB_TRY(cudaGetLastError());
+    } else {
+      // stage the 9 float planes of each lattice in the free population buffer (it holds at
+      // least 9 nx ny floats), then encode them into the current one
+      float* stage = static_cast<float*>(h->pops[(s + 1) & 1]);
+      for (int L = 0; L < h->nplanes / 9; ++L) {
+        LB_TRY(cudaMemcpyAsync(stage, static_cast<const float*>(src) + (size_t)9 * L * nx * ny,
+                               sizeof(float) * 9 * nx * ny, kind, h->stream));
+        float* M = L == 0 ? h->phi[s % 3] : L == 1 ? h->Um[s & 1] : h->rhom[s & 1];
+        int rc = with_storage(h, [&](auto tag) {
+          using S = decltype(tag);
+          encode_lattice_kernel<S><<<node_grid(h->C, blk), blk, 0, h->stream>>>(
+              h->C, stage, L, h->pops[s & 1], M);
+          return cuda_err(cudaGetLastError());
+        });
+        if (rc != LBMICE_OK) return rc;
+      }
+    }
   } else {
     if (bytes < sizeof(float) * nx * ny) return LBMICE_EINVAL;
     LB_TRY(cudaMemcpy2DAsync(h->phi[(s + 2) % 3], h->C.pitch * sizeof(float), src,
@@ -398,6 +545,8 @@ int lbmice_load(lbmice_t* h, int32_t which, const void* src, size_t bytes,
   if (!src_on_device) LB_TRY(cudaStreamSynchronize(h->stream));
   return LBMICE_OK;
 }
+
+extern "C" {
 
 int lbmice_stats(lbmice_t* h, double out[LBMICE_NSTATS]) {
   if (!h || !out) return LBMICE_EINVAL;
@@ -504,8 +653,8 @@ extern "C" int lbmice_stats_noalloc(const float* pops, const float* phi, const f
   C.pstride = (long long)pitch * ny;  // caller's layout: [plane][ny][pitch]
   C.rstride = pitch;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  stats_partial_kernel<<<nblocks, kStatThreads, 0, st>>>(C, flow, 0.5 * dx * dx, 0.5 * L_sat,
-                                                          pops, phi, phi_prev, partial);
+  stats_partial_kernel<F32><<<nblocks, kStatThreads, 0, st>>>(
+      C, flow, 0.5 * dx * dx, 0.5 * L_sat, pops, phi, phi_prev, nullptr, nullptr, partial);
   LB_TRY(cudaGetLastError());
   stats_final_kernel<<<1, 32, 0, st>>>(partial, nblocks, out);
   LB_TRY(cudaGetLastError());

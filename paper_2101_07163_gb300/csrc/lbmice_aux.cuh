@@ -20,23 +20,28 @@ __global__ void seed_kernel(int nx, int ny, double cx, double cy, double R0, dou
   const double p = tanh((R0 - sqrt(dx * dx + dy * dy)) / width);
   phi[i] = p;
   U[i] = U0;
-  rho[i] = 1.0;
-  const double liquid = 0.5 * (1.0 - p);
-  ux[i] = ux_in * liquid;
-  uy[i] = uy_in * liquid;
+  if (rho) {  // flow fields (absent without the flow lattice)
+    rho[i] = 1.0;
+    const double liquid = 0.5 * (1.0 - p);
+    ux[i] = ux_in * liquid;
+    uy[i] = uy_in * liquid;
+  }
 }
 
-// Populations at the equilibria of given moments, computed in double and stored as float:
-// h^eq (Eq. (e)) with the anisotropic flux of the E4 gradient of phi, g^eq (Sec. 2.2.2),
-// f^eq (Sec. 2.2.1). The stored phi and its history both become sum h.
-template <bool FLOW>
+// Populations at the equilibria of given moments, computed in double and stored in the
+// storage type: h^eq (Eq. (e)) with the anisotropic flux of the E4 gradient of phi, g^eq
+// (Sec. 2.2.2), f^eq (Sec. 2.2.1). The stored phi and its history both become sum h; with
+// 16-bit storage U and rho become sum g and sum f.
+template <bool FLOW, class S>
 __global__ void equilibrium_kernel(const Consts C, double Dphi3, double eps, double kN6eps,
                                    const double* __restrict__ phi0,
                                    const double* __restrict__ U0,
                                    const double* __restrict__ rho0,
                                    const double* __restrict__ ux0,
-                                   const double* __restrict__ uy0, float* __restrict__ pops,
-                                   float* __restrict__ phi_cur, float* __restrict__ phi_prev) {
+                                   const double* __restrict__ uy0, void* pops,
+                                   float* __restrict__ phi_cur, float* __restrict__ phi_prev,
+                                   float* __restrict__ U_cur, float* __restrict__ rho_cur) {
+  using ST = Storage<S>;
   const int X = blockIdx.x * blockDim.x + threadIdx.x;
   const int Y = blockIdx.y * blockDim.y + threadIdx.y;
   if (X >= C.nx || Y >= C.ny) return;
@@ -62,22 +67,76 @@ __global__ void equilibrium_kernel(const Consts C, double Dphi3, double eps, dou
   const double uy = uy0 ? uy0[i] : 0.0;
   const double uu = ux * ux + uy * uy;
   const long long o = (long long)Y * C.pitch + X;
-  const long long q0 = (long long)Y * C.rstride + X;
-  float hv[9];
+  typename ST::T* q0 = static_cast<typename ST::T*>(pops) + (long long)Y * C.rstride + X;
+  float hv[9], gv[9], fv[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const double w = wd_of(a);
     hv[a] = (float)(w * (ph - Dphi3 * cdot(a, Nx, Ny)));
-    pops[(PLANE_H + a) * C.pstride + q0] = hv[a];
     const double cu = cdot(a, ux, uy);
-    pops[(PLANE_G + a) * C.pstride + q0] = (float)(w * U * (1.0 + 3.0 * cu));
-    if (FLOW)
-      pops[(PLANE_F + a) * C.pstride + q0] =
-          (float)(w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+    gv[a] = (float)(w * U * (1.0 + 3.0 * cu));
+    fv[a] = (float)(w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
   }
   const float s = sum9(hv);
   phi_cur[o] = s;
   phi_prev[o] = s;
+  store9<S>(q0 + PLANE_H * C.pstride, C.pstride, s, hv);
+  const float Ug = ST::DEV ? sum9(gv) : 0.0f;
+  store9<S>(q0 + PLANE_G * C.pstride, C.pstride, Ug, gv);
+  if (ST::DEV) U_cur[o] = Ug;
+  if (FLOW) {
+    const float rf = ST::DEV ? sum9(fv) : 0.0f;
+    store9<S>(q0 + PLANE_F * C.pstride, C.pstride, rf, fv);
+    if (ST::DEV) rho_cur[o] = rf;
+  }
+}
+
+// Populations of lattice L (0 h, 1 g, 2 f) at node (X, Y), decoded to float.
+template <class S>
+__device__ __forceinline__ void node_lattice(const Consts& C, const void* pops, int L,
+                                             const float* phi, const float* U,
+                                             const float* rho, int X, int Y, float* out) {
+  using ST = Storage<S>;
+  const long long o = (long long)Y * C.pitch + X;
+  const typename ST::T* q0 =
+      static_cast<const typename ST::T*>(pops) + (long long)Y * C.rstride + X;
+  float M = 0.0f;
+  if (ST::DEV) M = L == 0 ? phi[o] : L == 1 ? U[o] : rho[o];
+  load9<S>(q0 + 9 * L * C.pstride, C.pstride, M, out);
+}
+
+// One decoded population plane (lattice L, direction a) into a contiguous [ny][nx] array.
+template <class S>
+__global__ void decode_plane_kernel(const Consts C, const void* pops, int L, int a,
+                                    const float* phi, const float* U, const float* rho,
+                                    float* __restrict__ out) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= C.nx || Y >= C.ny) return;
+  float v[9];
+  node_lattice<S>(C, pops, L, phi, U, rho, X, Y, v);
+  float r = v[0];
+#pragma unroll
+  for (int b = 1; b < 9; ++b) r = a == b ? v[b] : r;
+  out[(long long)Y * C.nx + X] = r;
+}
+
+// Encode one lattice from 9 contiguous float planes [9][ny][nx]; its moment goes to M.
+template <class S>
+__global__ void encode_lattice_kernel(const Consts C, const float* __restrict__ planes, int L,
+                                      void* pops, float* __restrict__ M) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= C.nx || Y >= C.ny) return;
+  const long long n = (long long)C.nx * C.ny, i = (long long)Y * C.nx + X;
+  float v[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) v[a] = planes[a * n + i];
+  const float m = sum9(v);
+  if (M) M[(long long)Y * C.pitch + X] = m;
+  typename Storage<S>::T* q0 =
+      static_cast<typename Storage<S>::T*>(pops) + (long long)Y * C.rstride + X;
+  store9<S>(q0 + 9 * L * C.pstride, C.pstride, m, v);
 }
 
 // phi = sum h of the current populations (after a checkpoint load).
@@ -96,14 +155,15 @@ __global__ void phi_from_pops_kernel(const Consts C, const float* __restrict__ p
 
 // Moment of the current state into a contiguous [ny][nx] float array.
 // which: 0 phi, 1 U, 2 rho, 3 u*_x, 4 u*_y, 5 phi history.
-__global__ void moment_kernel(const Consts C, int which, int flow,
-                              const float* __restrict__ pops, const float* __restrict__ phi,
-                              const float* __restrict__ phi_prev, float* __restrict__ out) {
+template <class S>
+__global__ void moment_kernel(const Consts C, int which, int flow, const void* pops,
+                              const float* __restrict__ phi, const float* __restrict__ phi_prev,
+                              const float* __restrict__ U, const float* __restrict__ rho,
+                              float* __restrict__ out) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x;
   const int Y = blockIdx.y * blockDim.y + threadIdx.y;
   if (X >= C.nx || Y >= C.ny) return;
   const long long o = (long long)Y * C.pitch + X;
-  const long long q0 = (long long)Y * C.rstride + X;
   float r = 0.0f;
   if (which == 0) {
     r = phi[o];
@@ -111,23 +171,21 @@ __global__ void moment_kernel(const Consts C, int which, int flow,
     r = phi_prev[o];
   } else if (which == 1) {
     float v[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_G + a) * C.pstride + q0];
+    node_lattice<S>(C, pops, 1, phi, U, rho, X, Y, v);
     r = sum9(v);
   } else if (!flow) {
     r = which == 2 ? 1.0f : 0.0f;
   } else {
     float v[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_F + a) * C.pstride + q0];
-    const float rho = sum9(v);
+    node_lattice<S>(C, pops, 2, phi, U, rho, X, Y, v);
+    const float rh = sum9(v);
     if (which == 2) {
-      r = rho;
+      r = rh;
     } else {
       const float ph = phi[o];
       const float onep = 1.0f + ph;
-      const float k = C.kdrag * rho * onep * onep * (1.0f - ph);
-      const float inv = 1.0f / (rho + 0.5f * k);
+      const float k = C.kdrag * rh * onep * onep * (1.0f - ph);
+      const float inv = 1.0f / (rh + 0.5f * k);
       const float sfac = 0.5f * (1.0f - ph);
       r = which == 3 ? sfac * (sumcx9(v) * inv) : sfac * (sumcy9(v) * inv);
     }
@@ -141,26 +199,25 @@ constexpr int kNStat = 5;
 // Block-level partial sums in double: solid area, mass, vapour invariant, sum phi, count of
 // non-finite nodes. One partial row per block; the final kernel adds rows in a fixed order,
 // so the result does not depend on scheduling.
+template <class S>
 __global__ void __launch_bounds__(kStatThreads)
     stats_partial_kernel(const Consts C, int flow, double area_w, double half_Lsat,
-                         const float* __restrict__ pops, const float* __restrict__ phi,
-                         const float* __restrict__ phi_prev, double* __restrict__ partial) {
+                         const void* pops, const float* __restrict__ phi,
+                         const float* __restrict__ phi_prev, const float* __restrict__ Um,
+                         const float* __restrict__ rhom, double* __restrict__ partial) {
   double acc[kNStat] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const long long n = (long long)C.nx * C.ny;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int Y = (int)(i / C.nx), X = (int)(i - (long long)Y * C.nx);
     const long long o = (long long)Y * C.pitch + X;
-    const long long q0 = (long long)Y * C.rstride + X;
     const float ph = phi[o];
     float v[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_G + a) * C.pstride + q0];
+    node_lattice<S>(C, pops, 1, phi, Um, rhom, X, Y, v);
     const float U = sum9(v);
     float rho = 1.0f;
     if (flow) {
-#pragma unroll
-      for (int a = 0; a < 9; ++a) v[a] = pops[(PLANE_F + a) * C.pstride + q0];
+      node_lattice<S>(C, pops, 2, phi, Um, rhom, X, Y, v);
       rho = sum9(v);
     }
     acc[0] += area_w * (1.0 + (double)ph);

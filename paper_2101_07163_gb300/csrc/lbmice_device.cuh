@@ -12,6 +12,8 @@
 // [q][ny][nx] uses the same formula with pstride = nx ny, rstride = nx.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -62,6 +64,66 @@ __device__ __forceinline__ T sumcx9(const T* v) {
 template <class T>
 __device__ __forceinline__ T sumcy9(const T* v) {
   return (v[2] - v[4]) + ((v[5] - v[7]) + (v[6] - v[8]));
+}
+
+// ---- storage of the populations ------------------------------------------------------
+// F32: the 9 populations of each lattice as float. F16 / BF16: the zeroth moment M of each
+// lattice as float (phi for h, U for g, rho for f, each in its own [ny][pitch] array) and the
+// 8 moving populations as 16-bit deviations d_a = p_a - w_a M; the rest population is rebuilt
+// as p_0 = M - sum_{a>0} p_a (summed in the pairing of sum9), so the populations sum back to
+// the stored M whatever the rounding of the deviations -- no systematic drift of mass or of
+// the vapour invariant. All arithmetic is FP32.
+struct F32 {};
+struct F16 {};
+struct BF16 {};
+template <class S> struct Storage;
+template <> struct Storage<F32> {
+  using T = float;
+  static constexpr bool DEV = false;
+  __device__ static __forceinline__ float load(const T* p) { return __ldg(p); }
+  __device__ static __forceinline__ T from_f(float v) { return v; }
+};
+template <> struct Storage<F16> {
+  using T = __half;
+  static constexpr bool DEV = true;
+  __device__ static __forceinline__ float load(const T* p) { return __half2float(__ldg(p)); }
+  __device__ static __forceinline__ T from_f(float v) { return __float2half_rn(v); }
+};
+template <> struct Storage<BF16> {
+  using T = __nv_bfloat16;
+  static constexpr bool DEV = true;
+  __device__ static __forceinline__ float load(const T* p) { return __bfloat162float(__ldg(p)); }
+  __device__ static __forceinline__ T from_f(float v) { return __float2bfloat16_rn(v); }
+};
+
+// Populations of one lattice at node offset q0 (plane a at q0 + a * pstride): stored values
+// for F32, or rebuilt from the moment M and the deviations for F16 / BF16.
+template <class S>
+__device__ __forceinline__ void load9(const typename Storage<S>::T* __restrict__ base,
+                                      long long pstride, float M, float* out) {
+  if constexpr (!Storage<S>::DEV) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) out[a] = Storage<S>::load(base + a * pstride);
+    return;
+  }
+#pragma unroll
+  for (int a = 1; a < 9; ++a)
+    out[a] = (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f) * M + Storage<S>::load(base + a * pstride);
+  out[0] = M - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
+}
+
+// Store the 9 populations p of one lattice whose zeroth moment is M (= sum p).
+template <class S>
+__device__ __forceinline__ void store9(typename Storage<S>::T* __restrict__ base,
+                                       long long pstride, float M, const float* p) {
+  if constexpr (!Storage<S>::DEV) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) base[a * pstride] = Storage<S>::from_f(p[a]);
+    return;
+  }
+#pragma unroll
+  for (int a = 1; a < 9; ++a)
+    base[a * pstride] = Storage<S>::from_f(p[a] - (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f) * M);
 }
 
 enum : int { BC_PERIODIC = 0, BC_INLET = 1, BC_OUTLET = 2, BC_FREESLIP = 3 };

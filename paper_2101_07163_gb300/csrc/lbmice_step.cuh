@@ -20,11 +20,15 @@
 namespace lbmice {
 
 struct StepPtrs {
-  const float* __restrict__ pin;      // populations at time n
-  float* __restrict__ pout;           // populations at time n + 1
-  const float* __restrict__ phi_n;    // phi^n
+  const void* pin;                    // populations at time n (storage type of the kernel)
+  void* pout;                         // populations at time n + 1
+  const float* __restrict__ phi_n;    // phi^n (the zeroth moment of h)
   const float* __restrict__ phi_nm1;  // phi^{n-1}
   float* __restrict__ phi_np1;        // phi^{n+1}
+  const float* __restrict__ U_n;      // 16-bit storage only: U^n, rho^n and their updates
+  float* __restrict__ U_np1;
+  const float* __restrict__ rho_n;
+  float* __restrict__ rho_np1;
 };
 
 template <int TX, int TY>
@@ -45,7 +49,7 @@ struct Tile {
 // coordinates (X, Y) in [-1, nx] x [-1, ny], and store its post-collision populations.
 // Ghost positions take the collision of the node their face rule maps them to (directions
 // mirrored across a free-slip wall), or the fixed inlet state.
-template <int TX, int TY, bool FLOW, bool OWN>
+template <int TX, int TY, bool FLOW, class S, bool OWN>
 __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& P, int X, int Y,
                                                int sx, int sy, const float* __restrict__ sphi,
                                                float* __restrict__ spost,
@@ -79,8 +83,10 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
       if (bc == BC_INLET && inlet < 0) inlet = face;
     }
   }
+  using ST = Storage<S>;
   const long long idx = (long long)my * C.pitch + mx;
-  const float* __restrict__ pin = P.pin + (long long)my * C.rstride + mx;
+  const typename ST::T* __restrict__ pin =
+      static_cast<const typename ST::T*>(P.pin) + (long long)my * C.rstride + mx;
 
   if (inlet >= 0) {
     // Inlet ghost: vapour at the inlet state, flow equilibrium at the adjacent density.
@@ -90,10 +96,13 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
                    : inlet == 2 ? C.uin_y[2] : C.uin_y[3];
     float rho = 1.0f;
     if (FLOW) {
-      float fv[9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) fv[a] = __ldg(pin + (PLANE_F + a) * C.pstride);
-      rho = sum9(fv);
+      if (ST::DEV) {
+        rho = __ldg(P.rho_n + idx);
+      } else {
+        float fv[9];
+        load9<S>(pin + PLANE_F * C.pstride, C.pstride, 0.0f, fv);
+        rho = sum9(fv);
+      }
     }
     const float uu = ux * ux + uy * uy;
 #pragma unroll
@@ -109,17 +118,15 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     return;
   }
 
-  // ---- moments at time n (Sec. 2.2) ----
-  float hv[9], gv[9], fv[9];
-#pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    hv[a] = __ldg(pin + (PLANE_H + a) * C.pstride);
-    gv[a] = __ldg(pin + (PLANE_G + a) * C.pstride);
-    if (FLOW) fv[a] = __ldg(pin + (PLANE_F + a) * C.pstride);
-  }
-  const float php = __ldg(P.phi_nm1 + idx);
+  // ---- populations and moments at time n (Sec. 2.2) ----
   const int pc = (ly + 1) * T::PW + (lx + 1);
   const float ph = sphi[pc];
+  float hv[9], gv[9], fv[9];
+  load9<S>(pin + PLANE_H * C.pstride, C.pstride, ph, hv);
+  load9<S>(pin + PLANE_G * C.pstride, C.pstride, ST::DEV ? __ldg(P.U_n + idx) : 0.0f, gv);
+  if (FLOW)
+    load9<S>(pin + PLANE_F * C.pstride, C.pstride, ST::DEV ? __ldg(P.rho_n + idx) : 0.0f, fv);
+  const float php = __ldg(P.phi_nm1 + idx);
   const float U = sum9(gv);
   float rho = 1.0f, jx = 0.0f, jy = 0.0f;
   if (FLOW) {
@@ -203,8 +210,9 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   sB[node] = 1.0f - inv_as2;
 }
 
-template <int TX, int TY, bool FLOW>
+template <int TX, int TY, bool FLOW, class S>
 __global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const StepPtrs P) {
+  using ST = Storage<S>;
   using T = Tile<TX, TY>;
   extern __shared__ float smem[];
   float* sphi = smem;
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const Step
   {
     const int X = x0 + tx, Y = y0 + ty;
     if (X <= C.nx && Y <= C.ny)
-      collide_source<TX, TY, FLOW, true>(C, P, X, Y, tx + 1, ty + 1, sphi, spost, sB, hown);
+      collide_source<TX, TY, FLOW, S, true>(C, P, X, Y, tx + 1, ty + 1, sphi, spost, sB, hown);
   }
   for (int r = tid; r < T::NRING; r += T::NT) {
     // ring order: bottom row, top row, then left and right columns
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const Step
     else { const int k = r - 2 * T::SW; sy = 1 + (k >> 1); sx = (k & 1) ? TX + 1 : 0; }
     const int X = x0 - 1 + sx, Y = y0 - 1 + sy;
     if (X >= -1 && X <= C.nx && Y >= -1 && Y <= C.ny)
-      collide_source<TX, TY, FLOW, false>(C, P, X, Y, sx, sy, sphi, spost, sB, nullptr);
+      collide_source<TX, TY, FLOW, S, false>(C, P, X, Y, sx, sy, sphi, spost, sB, nullptr);
   }
   __syncthreads();
 
@@ -253,17 +261,32 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const Step
   const int X = x0 + tx, Y = y0 + ty;
   if (X >= C.nx || Y >= C.ny) return;
   const long long idx = (long long)Y * C.pitch + X;
-  float* __restrict__ out = P.pout + (long long)Y * C.rstride + X;
-  float hn[9];
+  typename ST::T* __restrict__ out =
+      static_cast<typename ST::T*>(P.pout) + (long long)Y * C.rstride + X;
+  float hn[9], gn[9], fn[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const int src = (ty + 1 - cy_of(a)) * T::SW + (tx + 1 - cx_of(a));
     hn[a] = fmaf(hown[a], sB[src], spost[(PLANE_H + a) * T::SN + src]);
-    out[(PLANE_H + a) * C.pstride] = hn[a];
-    out[(PLANE_G + a) * C.pstride] = spost[(PLANE_G + a) * T::SN + src];
-    if (FLOW) out[(PLANE_F + a) * C.pstride] = spost[(PLANE_F + a) * T::SN + src];
+    gn[a] = spost[(PLANE_G + a) * T::SN + src];
+    if (FLOW) fn[a] = spost[(PLANE_F + a) * T::SN + src];
   }
-  P.phi_np1[idx] = sum9(hn);
+  const float phin = sum9(hn);
+  P.phi_np1[idx] = phin;
+  store9<S>(out + PLANE_H * C.pstride, C.pstride, phin, hn);
+  if (ST::DEV) {
+    const float Un = sum9(gn);
+    P.U_np1[idx] = Un;
+    store9<S>(out + PLANE_G * C.pstride, C.pstride, Un, gn);
+    if (FLOW) {
+      const float rn = sum9(fn);
+      P.rho_np1[idx] = rn;
+      store9<S>(out + PLANE_F * C.pstride, C.pstride, rn, fn);
+    }
+  } else {
+    store9<S>(out + PLANE_G * C.pstride, C.pstride, 0.0f, gn);
+    if (FLOW) store9<S>(out + PLANE_F * C.pstride, C.pstride, 0.0f, fn);
+  }
 }
 
 }  // namespace lbmice

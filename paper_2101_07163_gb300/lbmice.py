@@ -16,13 +16,15 @@ from .build import LIB
 
 OK, EINVAL, ECUDA, ENOMEM, ENONFINITE, EUNSTABLE, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FREESLIP = 0, 1, 2, 3
-PHI, U, RHO, UX, UY, PHI_PREV, POPS = 0, 1, 2, 3, 4, 5, 6
+PHI, U, RHO, UX, UY, PHI_PREV, POPS, STATE = 0, 1, 2, 3, 4, 5, 6, 7
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 NSTATS = 6
 STAT_NAMES = ("area", "mass", "vapour_invariant", "sum_phi", "nonfinite", "steps")
 
 EXPORTS = ("lbmice_params_default", "lbmice_create", "lbmice_init_seed", "lbmice_set_fields",
            "lbmice_step", "lbmice_fields", "lbmice_load", "lbmice_stats", "lbmice_sync",
-           "lbmice_steps_done", "lbmice_destroy", "lbmice_strerror")
+           "lbmice_steps_done", "lbmice_destroy", "lbmice_strerror", "lbmice_state_bytes",
+           "lbmice_stats_noalloc")
 
 
 class LbmiceError(RuntimeError):
@@ -42,7 +44,7 @@ class Params(ctypes.Structure):
         ("kappa_N", ctypes.c_double),
         ("U_in", ctypes.c_double), ("u_in", ctypes.c_double), ("nu", ctypes.c_double),
         ("bc", ctypes.c_int32 * 4), ("flow", ctypes.c_int32),
-        ("check_every", ctypes.c_int32),
+        ("check_every", ctypes.c_int32), ("storage", ctypes.c_int32),
     ]
 
 
@@ -74,6 +76,8 @@ def lib():
         L.lbmice_destroy.argtypes = [vp]
         L.lbmice_strerror.argtypes = [ctypes.c_int]
         L.lbmice_strerror.restype = ctypes.c_char_p
+        L.lbmice_state_bytes.argtypes = [vp]
+        L.lbmice_state_bytes.restype = sz
         _lib = L
     return _lib
 
@@ -92,7 +96,7 @@ def _check(rc: int, what: str):
 
 def make_params(nx, ny, *, dx=0.4, dt=0.008, W0=1.0, tau0=1.0, D=2.0, lam=0.0, L_sat=1.0,
                 eps=0.05, kappa_N=1.0, U_in=0.0, u_in=0.0, nu=0.016,
-                bc=(BC_PERIODIC,) * 4, flow=False, check_every=0) -> Params:
+                bc=(BC_PERIODIC,) * 4, flow=False, check_every=0, storage="f32") -> Params:
     p = Params()
     _check(lib().lbmice_params_default(ctypes.byref(p), int(nx), int(ny)), "params_default")
     p.dx, p.dt, p.W0, p.tau0 = dx, dt, W0, tau0
@@ -102,6 +106,7 @@ def make_params(nx, ny, *, dx=0.4, dt=0.008, W0=1.0, tau0=1.0, D=2.0, lam=0.0, L
         p.bc[i] = int(bc[i])
     p.flow = 1 if flow else 0
     p.check_every = int(check_every)
+    p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     return p
 
 
@@ -220,6 +225,16 @@ class Lattice:
         a = np.ascontiguousarray(arr, dtype=np.float32)
         _check(lib().lbmice_load(self._h, int(which), _ptr_host(a), a.nbytes, 0),
                "lbmice_load")
+
+    def state(self) -> np.ndarray:
+        """The exact state in its storage format (opaque bytes), for checkpoints."""
+        a = np.empty(int(lib().lbmice_state_bytes(self._h)), dtype=np.uint8)
+        _check(lib().lbmice_fields(self._h, STATE, _ptr_host(a), a.nbytes, 0), "lbmice_fields")
+        return a
+
+    def load_state(self, blob: np.ndarray):
+        a = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(lib().lbmice_load(self._h, STATE, _ptr_host(a), a.nbytes, 0), "lbmice_load")
 
     def stats(self) -> dict:
         out = (ctypes.c_double * NSTATS)()

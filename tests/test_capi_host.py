@@ -23,8 +23,8 @@ def declared_entry_points():
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
             text = open(os.path.join(ROOT, "include", fn)).read()
-            names |= set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(\w+)\s*\(", text,
-                                    re.M))
+            names |= set(re.findall(r"^\s*(?:int|int64_t|size_t|const char\*)\s+(\w+)\s*\(",
+                                    text, re.M))
     return sorted(names)
 
 
@@ -68,6 +68,7 @@ def test_params_default_and_strerror(L):
     (dict(flow=True, nu=0.0), lbmice.EUNSTABLE),
     (dict(flow=True, u_in=0.6, bc=(1, 2, 3, 3)), lbmice.EUNSTABLE),
     (dict(check_every=-1), lbmice.EINVAL),
+    (dict(storage=3), lbmice.EINVAL),
 ])
 def test_create_rejects_bad_parameters_without_a_gpu(L, change, code):
     kw = dict(nx=16, ny=16)
@@ -88,6 +89,7 @@ def test_null_handles_are_rejected(L):
     assert L.lbmice_set_fields(None, None, None, None, None, None, 0) == lbmice.EINVAL
     assert L.lbmice_sync(None) == lbmice.EINVAL
     assert L.lbmice_steps_done(None) == -1
+    assert L.lbmice_state_bytes(None) == 0
     assert L.lbmice_destroy(None) == 0
 
 

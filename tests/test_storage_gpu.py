@@ -1,0 +1,181 @@
+"""16-bit population storage (FP16 / BF16 deviations from the local rest state) against the
+FP64 oracle, and the FP32 storage on the same long-horizon gate.
+
+Storage keeps the zeroth moment of each lattice (phi, U, rho) in FP32 and the 8 moving
+populations as 16-bit deviations p_a - w_a M; all arithmetic is FP32. Bounds:
+  - one step: deviations are at most ~0.1 w_a on these states, so rounding them costs
+    ~0.1 w_a 2^-11 (FP16) or 2^-8 (BF16) per population: 2e-4 / 2e-3 absolute;
+  - 2000 steps of the 128 x 128 seed: an FP64 oracle whose deviations are rounded the same
+    way after every step drifts by 5e-5 (FP16) and 5e-4 (BF16) in phi on a 96 x 96 copy;
+    the bounds are 6x that;
+  - long horizon (spec gate): tip speed within 1% and solid area within 0.5%.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import LAT_F, LAT_G, LAT_H
+from paper_2101_07163_gb300 import lbmice
+from paper_2101_07163_gb300 import workloads as W
+from tests.helpers import tip_x
+
+pytestmark = pytest.mark.gpu
+
+ONE_STEP = {"f16": 2e-4, "bf16": 2e-3}
+SEED_2000 = {"f16": 3e-4, "bf16": 3e-3}
+
+
+def maxdiff(a, b):
+    return float(np.abs(np.asarray(a, dtype=np.float64) - b).max())
+
+
+def flow_workload(nx, ny, bc=(W.BC_PERIODIC,) * 4):
+    return W.Workload("s", nx, ny, 1, flow=True, eps=0.06, D=2.0, U0=0.35, U_in=0.3,
+                      u_in=0.03, nu=0.05, bc=bc, cx=nx * 0.45, cy=ny * 0.5, R0=8.0)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("bc", [(W.BC_PERIODIC,) * 4,
+                                (W.BC_INLET, W.BC_OUTLET, W.BC_FREESLIP, W.BC_FREESLIP)])
+def test_one_step_within_storage_rounding(storage, bc):
+    w = flow_workload(100, 76, bc)
+    f = W.perturbed_fields(w, 5, amp_phi=0.1, amp_U=0.05, amp_u=0.01)
+    lat = lbmice.Lattice(w.nx, w.ny, storage=storage, **w.params())
+    lat.set_fields(**f)
+    orc = oracle.Oracle(nx=w.nx, ny=w.ny, **w.params())
+    orc.set_fields(**f)
+    tol = ONE_STEP[storage]
+    for _ in range(2):
+        p = lat.pops().astype(np.float64)
+        assert maxdiff(p[0:9], orc.pops(LAT_H)) < tol
+        assert maxdiff(p[9:18], orc.pops(LAT_G)) < tol
+        assert maxdiff(p[18:27], orc.pops(LAT_F)) < tol
+        for which in (lbmice.PHI, lbmice.U, lbmice.RHO):
+            assert maxdiff(lat.field(which), orc.field(which)) < tol
+        lat.step(1)
+        orc.step(1)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_seed_128_2000_steps(storage):
+    w = W.C1
+    f = W.seed_fields(w)
+    lat = lbmice.Lattice(w.nx, w.ny, storage=storage, **w.params())
+    lat.set_fields(**f)
+    orc = oracle.Oracle(nx=w.nx, ny=w.ny, **w.params())
+    orc.set_fields(**f)
+    lat.step(w.steps)
+    orc.step(w.steps)
+    ph, pref = lat.field(lbmice.PHI), orc.field(oracle.PHI)
+    assert maxdiff(ph, pref) < SEED_2000[storage]
+    assert maxdiff(lat.field(lbmice.U), orc.field(oracle.U)) < SEED_2000[storage]
+    area, aref = (0.5 * (1 + ph.astype(np.float64))).sum(), (0.5 * (1 + pref)).sum()
+    assert abs(area - aref) / aref < SEED_2000[storage]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_moments_are_stored_exactly(storage):
+    # The rest population is rebuilt from the stored moment, so mass and the vapour invariant
+    # are kept to FP32 arithmetic however coarse the deviations are. FP32 collisions of a
+    # near-uniform state round the same way at every node, so the total may drift by up to
+    # about half an ulp per node and step: 300 steps x 6e-8 = 1.8e-5 relative. A 16-bit
+    # encoding that did not keep the moment would drift by ~1e-4 per step.
+    w = flow_workload(96, 80)
+    lat = lbmice.Lattice(w.nx, w.ny, storage=storage, **w.params())
+    lat.set_fields(**W.perturbed_fields(w, 6, amp_phi=0.2, amp_u=0.02))
+    s0 = lat.stats()
+    lat.step(300)
+    s = lat.stats()
+    assert s["nonfinite"] == 0
+    assert s["mass"] == pytest.approx(s0["mass"], rel=1.8e-5)
+    assert s["vapour_invariant"] == pytest.approx(s0["vapour_invariant"], rel=1.8e-5)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_state_checkpoint_restores_exactly(storage):
+    w = flow_workload(70, 50, (W.BC_INLET, W.BC_OUTLET, W.BC_FREESLIP, W.BC_FREESLIP))
+    f = W.perturbed_fields(w, 7)
+    a = lbmice.Lattice(w.nx, w.ny, storage=storage, **w.params())
+    a.set_fields(**f)
+    a.step(33)
+    blob = a.state()
+    a.step(64)
+    b = lbmice.Lattice(w.nx, w.ny, storage=storage, **w.params())
+    b.set_fields(**f)
+    b.step(7)  # a different parity of the internal buffers
+    b.load_state(blob)
+    b.step(64)
+    np.testing.assert_array_equal(a.state(), b.state())
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_population_export_import_round_trip(storage):
+    w = flow_workload(64, 48)
+    a = lbmice.Lattice(w.nx, w.ny, storage=storage, **w.params())
+    a.set_fields(**W.perturbed_fields(w, 8))
+    a.step(20)
+    pops, prev = a.pops(), a.field(lbmice.PHI_PREV)
+    b = lbmice.Lattice(w.nx, w.ny, storage=storage, **w.params())
+    b.set_fields(**W.perturbed_fields(w, 9))
+    b.load(lbmice.POPS, pops)
+    b.load(lbmice.PHI_PREV, prev)
+    assert maxdiff(b.pops(), pops) < ONE_STEP[storage] * 0.05
+    for which in (lbmice.PHI, lbmice.U, lbmice.RHO):
+        assert maxdiff(b.field(which), a.field(which)) < 1e-6
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_mirror_symmetry_survives_16_bit_storage(storage):
+    w = W.Workload("m", 64, 48, 1, flow=True, eps=0.07, nu=0.05)
+    lat = lbmice.Lattice(w.nx, w.ny, storage=storage, **w.params())
+    lat.set_fields(**W.mirror_fields(w, 21, amp=0.2))
+    lat.step(200)
+    ix, iy = (-np.arange(w.nx)) % w.nx, (-np.arange(w.ny)) % w.ny
+    for which in (lbmice.PHI, lbmice.U, lbmice.RHO):
+        a = lat.field(which)
+        np.testing.assert_array_equal(a, a[:, ix])
+        np.testing.assert_array_equal(a, a[iy, :])
+
+
+# ---- long horizon: tip speed and solid area (spec gate) ----------------------------
+
+LONG = W.C3.with_size(160, 160)  # the plate-regime physics (U0 = 0.5, eps = 0.05, D = 3)
+T1, T2 = 1500, 2500
+
+
+def tips_and_area(phi, w):
+    # the tip along +x and along the 60 degree ray is tracked through the +x row crossing
+    right = tip_x(phi, w.cy, w.cx, +1) - w.cx
+    left = w.cx - tip_x(phi, w.cy, w.cx, -1)
+    area = float((0.5 * (1.0 + phi.astype(np.float64))).sum()) * w.dx ** 2
+    return right, left, area
+
+
+@pytest.fixture(scope="module")
+def oracle_long():
+    w = LONG
+    o = oracle.Oracle(nx=w.nx, ny=w.ny, **w.params())
+    o.set_fields(**W.seed_fields(w))
+    o.step(T1)
+    a = tips_and_area(o.field(oracle.PHI), w)
+    o.step(T2 - T1)
+    b = tips_and_area(o.field(oracle.PHI), w)
+    return a, b
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_long_horizon_tip_speed_and_area(storage, oracle_long):
+    w = LONG
+    lat = lbmice.Lattice(w.nx, w.ny, storage=storage, **w.params())
+    lat.set_fields(**W.seed_fields(w))
+    lat.step(T1)
+    a = tips_and_area(lat.field(lbmice.PHI), w)
+    lat.step(T2 - T1)
+    b = tips_and_area(lat.field(lbmice.PHI), w)
+    (ra, la, Aa), (rb, lb, Ab) = oracle_long
+    v_ref = (rb - ra) / (T2 - T1)
+    v = (b[0] - a[0]) / (T2 - T1)
+    assert v_ref > 0
+    assert abs(v - v_ref) / v_ref < 0.01
+    assert abs(b[2] - Ab) / Ab < 0.005
