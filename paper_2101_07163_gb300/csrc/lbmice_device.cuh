@@ -104,12 +104,13 @@ __device__ __forceinline__ void load9(const typename Storage<S>::T* __restrict__
   if constexpr (!Storage<S>::DEV) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) out[a] = Storage<S>::load(base + a * pstride);
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int a = 1; a < 9; ++a)
-    out[a] = (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f) * M + Storage<S>::load(base + a * pstride);
-  out[0] = M - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
+    for (int a = 1; a < 9; ++a)
+      out[a] = (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f) * M + Storage<S>::load(base + a * pstride);
+    out[0] =
+        M - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
+  }
 }
 
 // Store the 9 populations p of one lattice whose zeroth moment is M (= sum p).
@@ -119,11 +120,11 @@ __device__ __forceinline__ void store9(typename Storage<S>::T* __restrict__ base
   if constexpr (!Storage<S>::DEV) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) base[a * pstride] = Storage<S>::from_f(p[a]);
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int a = 1; a < 9; ++a)
-    base[a * pstride] = Storage<S>::from_f(p[a] - (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f) * M);
+    for (int a = 1; a < 9; ++a)
+      base[a * pstride] = Storage<S>::from_f(p[a] - (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f) * M);
+  }
 }
 
 enum : int { BC_PERIODIC = 0, BC_INLET = 1, BC_OUTLET = 2, BC_FREESLIP = 3 };
