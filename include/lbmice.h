@@ -76,7 +76,7 @@ extern "C" {
 #define LBMICE_FIELD_STATE 7    /* the whole state in its storage format, opaque bytes
                                    (lbmice_state_bytes); loading it restores a run exactly */
 
-/* ---- storage of the populations (spec precision form; arithmetic is FP32) --------
+/* ---- storage of the populations (16-bit forms halve the traffic; arithmetic is FP32) ---
  * F32:  every population as float (224 B moved per node update with all three lattices).
  * F16, BF16: per lattice the zeroth moment (phi, U, rho) as float and the 8 moving
  *       populations as 16-bit deviations p_a - w_a M from the local rest state; the rest
@@ -186,6 +186,62 @@ int lbmice_destroy(lbmice_t* h);
 
 /* Static description of an error code. */
 const char* lbmice_strerror(int code);
+
+/* Name of the CUDA error behind the last LBMICE_ECUDA / LBMICE_ENOMEM returned on the calling
+ * thread ("none" if there was none); a static string. */
+const char* lbmice_last_error(void);
+
+/* ---- many grids in one launch --------------------------------------------------------------
+ * A batch advances many independent grids -- different sizes, supersaturations,
+ * anisotropies, inflows and faces -- with one kernel launch per time step for every tile
+ * shape in use (and per LBMICE_BATCH_MAX_PER_LAUNCH members of that shape), captured in CUDA
+ * graphs of 60 steps, instead of one launch per grid. Each launch carries its members'
+ * constants and buffer roles in its kernel parameters (no device-side list), one CTA per tile
+ * of the concatenated member tilings. Its members are ordinary handles: initialise, read and
+ * check them with the single-grid calls through lbmice_batch_member. All members share the
+ * flow flag and the storage, and advance in lockstep: lbmice_batch_step refuses (EINVAL) once
+ * a member was stepped on its own (re-initialising every member restarts them together).
+ * There is no device-side wait in the batched path.                                        */
+typedef struct lbmice_batch lbmice_batch_t;
+
+/* Tile shapes of 256 threads the batched kernel can use (autotuned per grid size). */
+#define LBMICE_SHAPE_32x8 0
+#define LBMICE_SHAPE_64x4 1
+#define LBMICE_SHAPE_16x16 2
+/* Members one batched launch can carry (its parameter block stays under 32 KB). */
+#define LBMICE_BATCH_MAX_PER_LAUNCH 128
+
+/* Create count member grids from params[0..count-1] on stream (as lbmice_create each), all
+ * with tile shape 32x8. Errors: EINVAL (count < 1, null, mixed flow or storage, any member's
+ * parameters), EUNSTABLE, ENOMEM, ECUDA; nothing is leaked on error. */
+int lbmice_batch_create(const lbmice_params* params, int32_t count, void* stream,
+                        lbmice_batch_t** out);
+
+/* Number of members, and a borrowed handle of member i (owned by the batch; do not
+ * destroy it, do not step it on its own). */
+int32_t lbmice_batch_size(const lbmice_batch_t* b);
+lbmice_t* lbmice_batch_member(lbmice_batch_t* b, int32_t i);
+
+/* Advance every member by nsteps: per step, one launch per tile shape in use and per
+ * LBMICE_BATCH_MAX_PER_LAUNCH members of that shape. Errors: EINVAL (members out of
+ * lockstep), ECUDA. Asynchronous. */
+int lbmice_batch_step(lbmice_batch_t* b, int64_t nsteps);
+
+/* Autotuner: for each distinct grid size, time steps_per_trial steps of those members with
+ * each tile shape (CUDA events) and keep the fastest. Every member is advanced by the same
+ * number of steps (written to *steps_taken), so the batch stays in lockstep; initialise the
+ * members again afterwards if the run must start from its initial state. shapes (optional,
+ * host, count entries) receives the chosen shape of each member. Synchronises the stream.
+ * Errors: EINVAL, ECUDA. */
+int lbmice_batch_autotune(lbmice_batch_t* b, int32_t steps_per_trial, int32_t* shapes,
+                          int64_t* steps_taken);
+
+/* Set the tile shape of member i (LBMICE_SHAPE_*); launches already queued keep the shapes
+ * they were given. Errors: EINVAL. */
+int lbmice_batch_set_shape(lbmice_batch_t* b, int32_t i, int32_t shape);
+
+/* Destroy the batch and all its members. Null is accepted. */
+int lbmice_batch_destroy(lbmice_batch_t* b);
 
 /* ---- diagnostics without allocation -------------------------------------------------------
  * The paper has no counterpart: this is a service of the library, not a step of the method.

@@ -2,11 +2,15 @@
 // derivation, device state, kernel launches and CUDA-graph replay of step chunks.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "../../include/lbmice.h"
 #include "lbmice_aux.cuh"
@@ -53,8 +57,12 @@ inline dim3 node_grid(const Consts& C, dim3 blk) {
   return dim3((C.nx + blk.x - 1) / blk.x, (C.ny + blk.y - 1) / blk.y);
 }
 
+// name of the last CUDA error this thread turned into an error code (lbmice_last_error)
+thread_local const char* g_last_cuda_error = "none";
+
 int cuda_err(cudaError_t e) {
   if (e == cudaSuccess) return LBMICE_OK;
+  g_last_cuda_error = cudaGetErrorName(e);
   return e == cudaErrorMemoryAllocation ? LBMICE_ENOMEM : LBMICE_ECUDA;
 }
 
@@ -162,7 +170,7 @@ int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
   P.U_np1 = h->Um[(s + 1) & 1];
   P.rho_n = h->rhom[s & 1];
   P.rho_np1 = h->rhom[(s + 1) & 1];
-  const dim3 grd((h->C.nx + kTX - 1) / kTX, (h->C.ny + kTY - 1) / kTY), blk(kTX, kTY);
+  const dim3 grd((h->C.nx + kTX - 1) / kTX, (h->C.ny + kTY - 1) / kTY), blk(kTX * kTY);
   return with_storage(h, [&](auto tag) {
     using S = decltype(tag);
     if (h->p.flow)
@@ -573,6 +581,8 @@ int lbmice_destroy(lbmice_t* h) {
   return cuda_err(e);
 }
 
+const char* lbmice_last_error(void) { return g_last_cuda_error; }
+
 const char* lbmice_strerror(int code) {
   switch (code) {
     case LBMICE_OK: return "ok";
@@ -660,3 +670,278 @@ extern "C" int lbmice_stats_noalloc(const float* pops, const float* phi, const f
   LB_TRY(cudaGetLastError());
   return LBMICE_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Batches: many member grids advanced by one launch per tile shape and step.
+// ---------------------------------------------------------------------------------------
+struct lbmice_batch {
+  std::vector<lbmice_t*> members;
+  std::vector<int> shape;             // tile shape id of each member
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;     // private stream used only to record graphs
+  int flow = 0, storage = 0;
+  std::unique_ptr<BatchLaunch> block; // host scratch for one launch's parameter block
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+// The batch has no step counter of its own: its members step together, and their common
+// count (which re-initialising every member resets) decides the buffer phase.
+int64_t batch_steps(const lbmice_batch_t* b) { return b->members[0]->step; }
+
+int member_tiles(const lbmice_t* m, int shape) {
+  const int tx = shape_tx(shape), ty = shape_ty(shape);
+  return ((m->C.nx + tx - 1) / tx) * ((m->C.ny + ty - 1) / ty);
+}
+
+// Buffer roles of step phase ph (step mod 6), as the single-grid path rotates them.
+StepPtrs step_ptrs(const lbmice_t* h, int ph) {
+  StepPtrs P;
+  P.pin = h->pops[ph & 1];
+  P.pout = h->pops[(ph + 1) & 1];
+  P.phi_n = h->phi[ph % 3];
+  P.phi_nm1 = h->phi[(ph + 2) % 3];
+  P.phi_np1 = h->phi[(ph + 1) % 3];
+  P.U_n = h->Um[ph & 1];
+  P.U_np1 = h->Um[(ph + 1) & 1];
+  P.rho_n = h->rhom[ph & 1];
+  P.rho_np1 = h->rhom[(ph + 1) & 1];
+  return P;
+}
+
+template <int TX, int TY>
+int launch_block(const lbmice_batch_t* b, int tiles, cudaStream_t st) {
+  return with_storage(b->members[0], [&](auto tag) {
+    using S = decltype(tag);
+    if (b->flow)
+      batch_step_kernel<TX, TY, true, S>
+          <<<tiles, TX * TY, Tile<TX, TY>::template smem_bytes<true>(), st>>>(*b->block);
+    else
+      batch_step_kernel<TX, TY, false, S>
+          <<<tiles, TX * TY, Tile<TX, TY>::template smem_bytes<false>(), st>>>(*b->block);
+    return cuda_err(cudaGetLastError());
+  });
+}
+
+// One step (phase ph) of the listed members: one launch per tile shape in use and per
+// kBatchMaxMembers members of that shape.
+int launch_members(lbmice_batch_t* b, const std::vector<int>& idx, int ph, cudaStream_t st) {
+  for (int s = 0; s < kNumShapes; ++s) {
+    size_t k = 0;
+    while (true) {
+      BatchLaunch& L = *b->block;
+      L.n = 0;
+      L.tile_start[0] = 0;
+      for (; k < idx.size() && L.n < kBatchMaxMembers; ++k) {
+        const int i = idx[k];
+        if (b->shape[i] != s) continue;
+        const lbmice_t* h = b->members[i];
+        BatchDesc& d = L.d[L.n];
+        d.C = h->C;
+        d.P = step_ptrs(h, ph);
+        d.tiles_x = (h->C.nx + shape_tx(s) - 1) / shape_tx(s);
+        d.pad_ = 0;
+        L.tile_start[L.n + 1] = L.tile_start[L.n] + member_tiles(h, s);
+        ++L.n;
+      }
+      if (L.n == 0) break;
+      const int tiles = L.tile_start[L.n];
+      const int rc = s == LBMICE_SHAPE_32x8   ? launch_block<32, 8>(b, tiles, st)
+                     : s == LBMICE_SHAPE_64x4 ? launch_block<64, 4>(b, tiles, st)
+                                              : launch_block<16, 16>(b, tiles, st);
+      if (rc != LBMICE_OK) return rc;
+      if (k >= idx.size()) break;
+    }
+  }
+  return LBMICE_OK;
+}
+
+void batch_release(lbmice_batch_t* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (lbmice_t* m : b->members) if (m) lbmice_destroy(m);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
+}
+
+std::vector<int> all_members(const lbmice_batch_t* b) {
+  std::vector<int> v(b->members.size());
+  for (size_t i = 0; i < v.size(); ++i) v[i] = (int)i;
+  return v;
+}
+
+bool in_lockstep(const lbmice_batch_t* b) {
+  for (const lbmice_t* m : b->members)
+    if (m->step != batch_steps(b)) return false;
+  return true;
+}
+
+void advance_members(lbmice_batch_t* b, int64_t n) {
+  for (lbmice_t* m : b->members) m->step += n;
+}
+
+void drop_graph(lbmice_batch_t* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbmice_batch_create(const lbmice_params* params, int32_t count, void* stream,
+                        lbmice_batch_t** out) {
+  if (!out) return LBMICE_EINVAL;
+  *out = nullptr;
+  if (!params || count < 1) return LBMICE_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (params[i].flow != params[0].flow || params[i].storage != params[0].storage)
+      return LBMICE_EINVAL;
+    const int rc = validate(params[i]);
+    if (rc != LBMICE_OK) return rc;
+  }
+  lbmice_batch_t* b = new (std::nothrow) lbmice_batch();
+  if (!b) return LBMICE_ENOMEM;
+  b->block.reset(new (std::nothrow) BatchLaunch());
+  if (!b->block) {
+    delete b;
+    return LBMICE_ENOMEM;
+  }
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->flow = params[0].flow;
+  b->storage = params[0].storage;
+  b->members.assign(count, nullptr);
+  b->shape.assign(count, LBMICE_SHAPE_32x8);
+  for (int i = 0; i < count; ++i) {
+    const int rc = lbmice_create(&params[i], stream, &b->members[i]);
+    if (rc != LBMICE_OK) {
+      batch_release(b);
+      return rc;
+    }
+  }
+  const cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    batch_release(b);
+    return cuda_err(e);
+  }
+  *out = b;
+  return LBMICE_OK;
+}
+
+int32_t lbmice_batch_size(const lbmice_batch_t* b) { return b ? (int32_t)b->members.size() : 0; }
+
+lbmice_t* lbmice_batch_member(lbmice_batch_t* b, int32_t i) {
+  if (!b || i < 0 || i >= (int32_t)b->members.size()) return nullptr;
+  return b->members[i];
+}
+
+int lbmice_batch_set_shape(lbmice_batch_t* b, int32_t i, int32_t shape) {
+  if (!b || i < 0 || i >= (int32_t)b->members.size() || shape < 0 || shape >= kNumShapes)
+    return LBMICE_EINVAL;
+  b->shape[i] = shape;
+  drop_graph(b);  // launches already queued keep the parameter blocks they were given
+  return LBMICE_OK;
+}
+
+int lbmice_batch_step(lbmice_batch_t* b, int64_t nsteps) {
+  if (!b || nsteps < 0) return LBMICE_EINVAL;
+  if (!in_lockstep(b)) return LBMICE_EINVAL;
+  const std::vector<int> all = all_members(b);
+  int64_t left = nsteps;
+  while (left > 0) {
+    if (batch_steps(b) % 6 == 0 && left >= kGraphSteps) {
+      if (!b->graph) {
+        cudaGraph_t g = nullptr;
+        LB_TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+        int rc = LBMICE_OK;
+        for (int s = 0; s < kGraphSteps && rc == LBMICE_OK; ++s)
+          rc = launch_members(b, all, s % 6, b->capture);
+        cudaError_t e = cudaStreamEndCapture(b->capture, &g);
+        if (rc != LBMICE_OK) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return cuda_err(e);
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { b->graph = nullptr; return cuda_err(e); }
+      }
+      LB_TRY(cudaGraphLaunch(b->graph, b->stream));
+      advance_members(b, kGraphSteps);
+      left -= kGraphSteps;
+    } else {
+      const int rc = launch_members(b, all, (int)(batch_steps(b) % 6), b->stream);
+      if (rc != LBMICE_OK) return rc;
+      advance_members(b, 1);
+      left -= 1;
+    }
+  }
+  return LBMICE_OK;
+}
+
+int lbmice_batch_autotune(lbmice_batch_t* b, int32_t steps_per_trial, int32_t* shapes,
+                          int64_t* steps_taken) {
+  if (!b || steps_per_trial < 1) return LBMICE_EINVAL;
+  if (!in_lockstep(b)) return LBMICE_EINVAL;
+  const int n = (int)b->members.size();
+  drop_graph(b);
+  // size classes
+  std::vector<std::pair<int, int>> classes;
+  for (const lbmice_t* m : b->members) {
+    const std::pair<int, int> key(m->C.nx, m->C.ny);
+    if (std::find(classes.begin(), classes.end(), key) == classes.end()) classes.push_back(key);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LB_TRY(cudaEventCreate(&e0));
+  LB_TRY(cudaEventCreate(&e1));
+  int64_t taken = 0;
+  int rc = LBMICE_OK;
+  for (const auto& cls : classes) {
+    std::vector<int> in, rest;
+    for (int i = 0; i < n; ++i)
+      (b->members[i]->C.nx == cls.first && b->members[i]->C.ny == cls.second ? in : rest)
+          .push_back(i);
+    float best = 0.0f;
+    int best_shape = 0;
+    for (int s = 0; s < kNumShapes && rc == LBMICE_OK; ++s) {
+      for (int i : in) b->shape[i] = s;
+      // one untimed step, then the timed steps of this class; the other members take the
+      // same number of steps untimed, so the batch stays in lockstep
+      const int64_t base = batch_steps(b);
+      for (int k = 0; k <= steps_per_trial && rc == LBMICE_OK; ++k) {
+        if (k == 1) rc = cuda_err(cudaEventRecord(e0, b->stream));
+        if (rc == LBMICE_OK) rc = launch_members(b, in, (int)((base + k) % 6), b->stream);
+      }
+      if (rc == LBMICE_OK) rc = cuda_err(cudaEventRecord(e1, b->stream));
+      for (int k = 0; k <= steps_per_trial && rc == LBMICE_OK && !rest.empty(); ++k)
+        rc = launch_members(b, rest, (int)((base + k) % 6), b->stream);
+      if (rc == LBMICE_OK) rc = cuda_err(cudaStreamSynchronize(b->stream));
+      float ms = 0.0f;
+      if (rc == LBMICE_OK) rc = cuda_err(cudaEventElapsedTime(&ms, e0, e1));
+      if (rc == LBMICE_OK) {
+        advance_members(b, steps_per_trial + 1);
+        taken += steps_per_trial + 1;
+        if (s == 0 || ms < best) {
+          best = ms;
+          best_shape = s;
+        }
+      }
+    }
+    for (int i : in) b->shape[i] = best_shape;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LBMICE_OK) return rc;
+  if (shapes)
+    for (int i = 0; i < n; ++i) shapes[i] = b->shape[i];
+  if (steps_taken) *steps_taken = taken;
+  return LBMICE_OK;
+}
+
+int lbmice_batch_destroy(lbmice_batch_t* b) {
+  if (!b) return LBMICE_OK;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  batch_release(b);
+  return cuda_err(e);
+}
+
+}  // extern "C"

@@ -15,6 +15,7 @@
 // phi^{n+1} out; halo re-reads hit L2.
 #pragma once
 
+#include "../../include/lbmice.h"
 #include "lbmice_device.cuh"
 
 namespace lbmice {
@@ -266,17 +267,18 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   sB[node] = 1.0f - inv_as2;
 }
 
+// One TX x TY tile with origin (x0, y0), computed by the TX * TY threads of the CTA (thread
+// tid owns node (x0 + tid % TX, y0 + tid / TX)). smem holds Tile<TX, TY>::smem_bytes.
 template <int TX, int TY, bool FLOW, class S>
-__global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const StepPtrs P) {
+__device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, int x0, int y0,
+                                          float* smem) {
   using ST = Storage<S>;
   using T = Tile<TX, TY>;
-  extern __shared__ float smem[];
   float* sphi = smem;
   float* spost = sphi + T::PN;
   float* sB = spost + (FLOW ? 27 : 18) * T::SN;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * TX + tx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
 
   // ---- A: phi^n with a two-node halo ----
   for (int i = tid; i < T::PN; i += T::NT) {
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const Step
 
   // ---- C: pull, Eq. (d) for h, write populations and phi^{n+1} ----
   const int X = x0 + tx, Y = y0 + ty;
-  if (X >= C.nx || Y >= C.ny) return;
+  if (X >= C.nx || Y >= C.ny) return;  // (this thread has no node in this tile)
   const long long idx = (long long)Y * C.pitch + X;
   typename ST::T* __restrict__ out =
       static_cast<typename ST::T*>(P.pout) + (long long)Y * C.rstride + X;
@@ -354,6 +356,60 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const Step
       store9<S>(out + PLANE_F * C.pstride, C.pstride, rn, fn);
     }
   }
+}
+
+template <int TX, int TY, bool FLOW, class S>
+__global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const StepPtrs P) {
+  extern __shared__ float smem[];
+  step_tile<TX, TY, FLOW, S>(C, P, blockIdx.x * TX, blockIdx.y * TY, smem);
+}
+
+// ---- many grids in one launch ----------------------------------------------------------
+// Tile shapes of 256 threads that the batched kernel can use for a member grid; the
+// autotuner picks one per grid size. Each shape is its own kernel instantiation, launched
+// with exactly its shared memory (a larger request shrinks the L1 left for the pull).
+constexpr int kNumShapes = 3;
+__host__ __device__ constexpr int shape_tx(int s) { return s == 0 ? 32 : s == 1 ? 64 : 16; }
+__host__ __device__ constexpr int shape_ty(int s) { return s == 0 ? 8 : s == 1 ? 4 : 16; }
+
+// One member grid of a batched launch: its constants, the buffer roles of this step and its
+// tile count per row in the launch's shape.
+struct BatchDesc {
+  Consts C;
+  StepPtrs P;
+  int tiles_x;
+  int pad_;
+};
+
+// Parameter block of one batched launch: up to kBatchMaxMembers grids, list position k owning
+// tiles tile_start[k] .. tile_start[k+1]-1 (row-major within the grid). It travels as a
+// __grid_constant__ kernel parameter, so the descriptors sit in the constant bank (no device
+// buffer to upload, nothing to race with launches still queued) and the block stays within
+// the 32,764-byte parameter limit.
+constexpr int kBatchMaxMembers = LBMICE_BATCH_MAX_PER_LAUNCH;
+struct BatchLaunch {
+  int n;
+  int tile_start[kBatchMaxMembers + 1];
+  BatchDesc d[kBatchMaxMembers];
+};
+static_assert(sizeof(BatchLaunch) <= 32764, "kernel parameter limit");
+
+// One CTA per tile of a batched launch: binary search for the owning grid, then the
+// single-grid tile code. A tile beyond its grid (a malformed block) is skipped.
+template <int TX, int TY, bool FLOW, class S>
+__global__ void __launch_bounds__(TX* TY, 4) batch_step_kernel(const __grid_constant__ BatchLaunch L) {
+  extern __shared__ float smem[];
+  const int t = blockIdx.x;
+  int lo = 0, hi = L.n - 1;  // last list position whose first tile is <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  const BatchDesc& d = L.d[lo];
+  const int local = t - L.tile_start[lo];
+  const int tyi = local / d.tiles_x, txi = local - tyi * d.tiles_x;
+  if (local < 0 || tyi * TY >= d.C.ny) return;
+  step_tile<TX, TY, FLOW, S>(d.C, d.P, txi * TX, tyi * TY, smem);
 }
 
 }  // namespace lbmice

@@ -24,13 +24,21 @@ STAT_NAMES = ("area", "mass", "vapour_invariant", "sum_phi", "nonfinite", "steps
 EXPORTS = ("lbmice_params_default", "lbmice_create", "lbmice_init_seed", "lbmice_set_fields",
            "lbmice_step", "lbmice_fields", "lbmice_load", "lbmice_stats", "lbmice_sync",
            "lbmice_steps_done", "lbmice_destroy", "lbmice_strerror", "lbmice_state_bytes",
-           "lbmice_stats_noalloc")
+           "lbmice_stats_noalloc", "lbmice_batch_create", "lbmice_batch_size",
+           "lbmice_batch_member", "lbmice_batch_step", "lbmice_batch_autotune",
+           "lbmice_batch_set_shape", "lbmice_batch_destroy", "lbmice_last_error")
 
 
 class LbmiceError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
-        super().__init__(f"{what}: {strerror(code)} ({code})")
+        detail = ""
+        if code in (ECUDA, ENOMEM):
+            try:
+                detail = " [" + lib().lbmice_last_error().decode() + "]"
+            except Exception:
+                pass
+        super().__init__(f"{what}: {strerror(code)} ({code}){detail}")
 
 
 class Params(ctypes.Structure):
@@ -78,6 +86,8 @@ def lib():
         L.lbmice_strerror.restype = ctypes.c_char_p
         L.lbmice_state_bytes.argtypes = [vp]
         L.lbmice_state_bytes.restype = sz
+        L.lbmice_last_error.argtypes = []
+        L.lbmice_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -240,3 +250,116 @@ class Lattice:
         out = (ctypes.c_double * NSTATS)()
         _check(lib().lbmice_stats(self._h, out), "lbmice_stats")
         return dict(zip(STAT_NAMES, list(out)))
+
+
+SHAPES = {0: (32, 8), 1: (64, 4), 2: (16, 16)}
+BATCH_MAX_PER_LAUNCH = 128  # members one batched launch carries (LBMICE_BATCH_MAX_PER_LAUNCH)
+
+
+class _Member(Lattice):
+    """A member grid of a Batch (borrowed handle: the batch owns and destroys it)."""
+
+    def __init__(self, batch, i, h, params):
+        self.nx, self.ny = int(params.nx), int(params.ny)
+        self.params = params
+        self.flow = bool(params.flow)
+        self.nplanes = 27 if self.flow else 18
+        self._stream = batch.stream
+        self.device = batch.device
+        self._h = ctypes.c_void_p(h)
+        self._batch = batch
+
+    def close(self):  # owned by the batch
+        self._h = None
+
+    def step(self, n: int = 1):
+        raise RuntimeError("members advance through Batch.step")
+
+
+class Batch:
+    """Many grids advanced together, one kernel launch per step for each tile shape in use
+    (include/lbmice.h, lbmice_batch_*). ``configs``: a list of keyword dicts, each with nx, ny
+    and the make_params keywords of one member; all share flow and storage."""
+
+    def __init__(self, configs, *, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("lbmice needs a CUDA GPU; there is no CPU fallback")
+        L = lib()
+        L.lbmice_batch_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+        L.lbmice_batch_size.argtypes = [ctypes.c_void_p]
+        L.lbmice_batch_size.restype = ctypes.c_int32
+        L.lbmice_batch_member.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        L.lbmice_batch_member.restype = ctypes.c_void_p
+        L.lbmice_batch_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        L.lbmice_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int64)]
+        L.lbmice_batch_set_shape.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
+        L.lbmice_batch_destroy.argtypes = [ctypes.c_void_p]
+        cfgs = [dict(c) for c in configs]
+        n = len(cfgs)
+        arr = (Params * n)()
+        for i, c in enumerate(cfgs):
+            nx, ny = c.pop("nx"), c.pop("ny")
+            arr[i] = make_params(nx, ny, **c)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = self.stream.device
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(L.lbmice_batch_create(arr, n, ctypes.c_void_p(self.stream.cuda_stream),
+                                         ctypes.byref(h)), "lbmice_batch_create")
+        self._h = h
+        self._params = arr
+        self.members = [_Member(self, i, L.lbmice_batch_member(h, i), arr[i]) for i in range(n)]
+        self.shapes = [0] * n
+
+    def __len__(self):
+        return len(self.members)
+
+    def __getitem__(self, i) -> Lattice:
+        return self.members[i]
+
+    def step(self, n: int = 1):
+        _check(lib().lbmice_batch_step(self._h, int(n)), "lbmice_batch_step")
+
+    def autotune(self, steps_per_trial: int = 6):
+        """Pick a tile shape per grid size; returns (shapes, steps_taken)."""
+        n = len(self.members)
+        shapes = (ctypes.c_int32 * n)()
+        taken = ctypes.c_int64()
+        _check(lib().lbmice_batch_autotune(self._h, int(steps_per_trial), shapes,
+                                           ctypes.byref(taken)), "lbmice_batch_autotune")
+        self.shapes = list(shapes)
+        return list(shapes), int(taken.value)
+
+    def set_shape(self, i: int, shape: int):
+        _check(lib().lbmice_batch_set_shape(self._h, int(i), int(shape)), "lbmice_batch_set_shape")
+        self.shapes[i] = int(shape)
+
+    @property
+    def launches_per_step(self) -> int:
+        """Kernel launches of one batched step: per tile shape in use, one per
+        BATCH_MAX_PER_LAUNCH members of that shape."""
+        return sum(-(-self.shapes.count(s) // BATCH_MAX_PER_LAUNCH) for s in SHAPES)
+
+    @property
+    def nodes(self) -> int:
+        return sum(m.nx * m.ny for m in self.members)
+
+    def sync(self):
+        self.members[0].sync()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m.close()
+            _check(lib().lbmice_batch_destroy(self._h), "lbmice_batch_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

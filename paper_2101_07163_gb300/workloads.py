@@ -140,3 +140,30 @@ def mirror_fields(w: Workload, seed: int, amp: float = 0.05) -> dict:
     f["ux"] = 0.2 * amp * sym(even_x=False)
     f["uy"] = 0.2 * amp * sym(even_y=False)
     return f
+
+
+# ---- batched sweep: 96 independent crystals of uneven sizes --------------------------------
+C4_SIDES = (256, 384, 512, 768, 1024)
+
+
+def batch_sweep(count: int = 96, seed: int = 2101, sides=C4_SIDES, steps: int = 10000):
+    """Members of the batched sweep: square grids drawn uniformly from `sides`,
+    U0 ~ U[0.1, 0.6], eps ~ U[0.02, 0.08], inflow u ~ U[0, 0.03] along a random axis (inlet
+    upstream, zero-gradient outlet downstream, free-slip on the two other faces), seed radius
+    6 at the centre; numpy PCG64 with the given seed."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sides))
+        U0 = float(rng.uniform(0.1, 0.6))
+        eps = float(rng.uniform(0.02, 0.08))
+        u = float(rng.uniform(0.0, 0.03))
+        axis = int(rng.integers(0, 4))  # inflow towards +x, -x, +y, -y
+        bc = [BC_FREESLIP] * 4
+        inlet = {0: 0, 1: 1, 2: 2, 3: 3}[axis]
+        outlet = inlet ^ 1
+        bc[inlet], bc[outlet] = BC_INLET, BC_OUTLET
+        out.append(Workload(f"sweep{i:02d}_{n}", n, n, steps, D=2.0, eps=eps, U0=U0, U_in=U0,
+                            u_in=u, nu=0.016, bc=tuple(bc), flow=True, cx=n / 2, cy=n / 2,
+                            R0=6.0))
+    return out

@@ -8,7 +8,7 @@ populations as 16-bit deviations p_a - w_a M; all arithmetic is FP32. Bounds:
   - 2000 steps of the 128 x 128 seed: an FP64 oracle whose deviations are rounded the same
     way after every step drifts by 5e-5 (FP16) and 5e-4 (BF16) in phi on a 96 x 96 copy;
     the bounds are 6x that;
-  - long horizon (spec gate): tip speed within 1% and solid area within 0.5%.
+  - long horizon: tip speed within 1% and solid area within 0.5% of the FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -137,7 +137,7 @@ def test_mirror_symmetry_survives_16_bit_storage(storage):
         np.testing.assert_array_equal(a, a[iy, :])
 
 
-# ---- long horizon: tip speed and solid area (spec gate) ----------------------------
+# ---- long horizon: tip speed and solid area -----------------------------------------------
 
 LONG = W.C3.with_size(160, 160)  # the plate-regime physics (U0 = 0.5, eps = 0.05, D = 3)
 T1, T2 = 1500, 2500
