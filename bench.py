@@ -55,6 +55,8 @@ def parse():
                     help="16-bit storage legs timed after the FP32 leg ('' for none)")
     ap.add_argument("--batch-steps", type=int, default=120,
                     help="steps of the 96-crystal batched sweep leg (0: skip)")
+    ap.add_argument("--batch-count", type=int, default=96,
+                    help="crystals of the batched sweep (profiling runs: the first n of the 96)")
     return ap.parse_args()
 
 
@@ -155,9 +157,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(nodes: int):
-    """DRAM bytes per launch from the committed ncu summary ("key = value" lines), scaled
-    to this grid by the node count; None once the kernel source has changed since."""
+def profiled_traffic(nodes: int, kernel: str = "f32"):
+    """DRAM bytes of `nodes` grid nodes through one benchmarked kernel ("f32", "f16",
+    "batch"), from the committed ncu summary ("key = value" lines, bytes per node); None
+    when that kernel was not captured or its source has changed since."""
     rec = {}
     try:
         with open(PROFILE_TRAFFIC) as fh:
@@ -168,11 +171,13 @@ def profiled_traffic(nodes: int):
                     rec[k] = v
     except OSError:
         return None, None
-    if "dram_bytes_per_node" not in rec:
+    key = kernel + ".dram_bytes_per_node"
+    if key not in rec:
         return None, None
+    info = {"source": rec.get(kernel + ".source")}
     if rec.get("kernel_source_sha256_16") != kernel_source_hash():
-        return None, rec
-    return float(rec["dram_bytes_per_node"]) * nodes, rec
+        return None, info
+    return float(rec[key]) * nodes, info
 
 
 def measured_peak():
@@ -240,7 +245,7 @@ def run_batched(args, stream, dist):
     (CUDA graphs), against the same members stepped one grid at a time."""
     import torch
     from paper_2101_07163_gb300 import lbmice
-    ws = W.batch_sweep()
+    ws = W.batch_sweep(count=args.batch_count)
     b = lbmice.Batch([dict(nx=w.nx, ny=w.ny, **w.params()) for w in ws], stream=stream)
     for m, w in zip(b.members, ws):
         m.init_seed(w.cx, w.cy, w.R0, w.U0)
@@ -271,7 +276,7 @@ def run_batched(args, stream, dist):
     by_side = {}
     for w, s in zip(ws, shapes):
         by_side.setdefault(str(w.nx), "%dx%d" % lbmice.SHAPES[s])
-    out = {"workload": "batch_sweep: 96 crystals, sides {256..1024}, PCG64 seed 2101",
+    out = {"workload": "batch_sweep: %d crystals, sides {256..1024}, PCG64 seed 2101" % len(ws),
            "members": len(ws), "nodes": int(b.nodes), "steps": K, "ms": ms, "ms_seq": ms_seq,
            "tile_shape_by_side": by_side, "finite": bool(finite),
            "gpu_launches_per_step": b.launches_per_step}
@@ -403,8 +408,13 @@ def run_ours(args):
             batched.pop("ms_seq") * 1e-3) / 1e6
         ach = ALGO_BYTES_PER_LUP[("f32", 3)] * batched["nodes"] / (
             batched["ms"] / batched["steps"] * 1e-3) / 1e9
+        btraffic, brec = profiled_traffic(batched["nodes"], "batch")
         batched["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                               "frac": ach / peak, "algorithmic_bytes_per_lup": 224}
+                               "frac": ach / peak, "traffic": btraffic,
+                               "algorithmic_bytes_per_lup": 224,
+                               "kernel": "lbmice::batch_step_kernel<32,8,flow,F32>"}
+        if brec is not None:
+            batched["roofline"]["traffic_source"] = brec.get("source")
         batched["ms_per_step"] = batched.pop("ms") / batched["steps"]
         batched["unit"] = "MLUPS"
         line["batched"] = batched
@@ -421,7 +431,8 @@ def run_ours(args):
                                     "algorithmic_bytes_per_lup":
                                         ALGO_BYTES_PER_LUP[(st, w.lattices)],
                                     "design_bytes_per_lup":
-                                        DESIGN_BYTES_PER_LUP[(st, w.lattices)]}}
+                                        DESIGN_BYTES_PER_LUP[(st, w.lattices)],
+                                    "traffic": profiled_traffic(nodes, st)[0]}}
         line["storage_legs"] = out
 
     # ---- CPU baseline and error against the FP64 oracle, rank 0, N = 1 only ----
