@@ -74,6 +74,7 @@ def lib():
         L.orc_gradient_periodic.argtypes = [dp, i32, i32, dp, dp]
         L.orc_anisotropy.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, dp]
+        L.orc_grad_run.argtypes = [ctypes.POINTER(OrcParams)] + [dp] * 10 + [i64, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -184,3 +185,30 @@ def anisotropy(gx: float, gy: float, eps: float, kappa_N: float = 1.0):
     out = np.zeros(3)
     lib().orc_anisotropy(float(gx), float(gy), float(eps), float(kappa_N), _dp(out))
     return float(out[0]), float(out[1]), float(out[2])
+
+
+GRAD_KEYS = ("eps", "D", "lambda", "init")
+
+
+def grad_run(params: OrcParams, fields: dict, nsteps: int, wphi, wU, dfields: dict | None = None):
+    """Exact forward-mode derivatives of L = sum(wphi * phi_T + wU * U_T) after ``nsteps``
+    steps from the equilibrium state of ``fields`` (keys phi, U and optionally rho, ux, uy),
+    with respect to eps, D (through D_lat and, if lambda is not given, the beta = 0 lambda),
+    lambda alone, and the initial moments along ``dfields`` (same keys; missing = 0).
+    Returns {"L": ..., "eps": ..., "D": ..., "lambda": ..., "init": ...}."""
+    n = params.nx * params.ny
+    dfields = dfields or {}
+    f = {k: _f64(fields.get(k)) for k in ("phi", "U", "rho", "ux", "uy")}
+    df = {}
+    for k in ("phi", "U", "rho", "ux", "uy"):
+        v = dfields.get(k)
+        df[k] = _f64(v) if v is not None else (np.zeros(n) if k in ("phi", "U") else None)
+    w1, w2 = _f64(wphi), _f64(wU)
+    out = np.zeros(5)
+    rc = lib().orc_grad_run(ctypes.byref(params), _dp(f["phi"]), _dp(f["U"]), _dp(f["rho"]),
+                            _dp(f["ux"]), _dp(f["uy"]), _dp(df["phi"]), _dp(df["U"]),
+                            _dp(df["rho"]), _dp(df["ux"]), _dp(df["uy"]), int(nsteps),
+                            _dp(w1), _dp(w2), _dp(out))
+    if rc != 0:
+        raise ValueError("oracle rejected the gradient run")
+    return dict(zip(("L",) + GRAD_KEYS, out.tolist()))

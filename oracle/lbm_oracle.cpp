@@ -118,6 +118,9 @@ template <class T>
 struct Oracle {
   orc_params p;
   Derived d;
+  // The parameters the gradient of the method is taken with respect to, in the scalar type
+  // of the run (for T = double they are exactly p.eps, d.Dlat and d.lambda).
+  T eps = T(0.0), Dlat = T(0.0), lambda = T(0.0);
   int nx = 0, ny = 0;
   size_t n = 0;
   // Pre-collision populations at time t, one array per direction, node index y*nx + x.
@@ -204,8 +207,8 @@ void grad_e4(T pE, T pW, T pN, T pS, T pNE, T pNW, T pSE, T pSW, T* gx, T* gy) {
 // a_s through theta = atan2(g_y, g_x) gives |g|^2 da_s/dg = 6 eps sin(6 theta) (g_y, -g_x),
 // so N = kappa_N a_s 6 eps sin(6 theta) (g_y, -g_x). N is linear in g and carries its units.
 // ---------------------------------------------------------------------------------------
-template <class T>
-void anisotropy(T gx, T gy, double eps, double kappa_N, T* as, T* Nx, T* Ny) {
+template <class T, class P>
+void anisotropy(T gx, T gy, P eps, double kappa_N, T* as, T* Nx, T* Ny) {
   const T s = gx * gx + gy * gy;
   if (!(s > kGradEps)) {
     *as = T(1.0);
@@ -359,10 +362,10 @@ void collide(Oracle<T>* o) {
       // Gradient, anisotropy and the phase-field relaxation time (Sec. 2.2.3).
       T gx, gy, as, Nx, Ny;
       gradient_at(*o, phi, x, y, &gx, &gy);
-      anisotropy(gx, gy, p.eps, p.kappa_N, &as, &Nx, &Ny);
+      anisotropy(gx, gy, o->eps, p.kappa_N, &as, &Nx, &Ny);
       const T a2 = as * as;
       const T eta = 3.0 * a2 * d.Dphi + 0.5;
-      const T Qphi = ph - ph * ph * ph + d.lambda * U * (1.0 - ph * ph) * (1.0 - ph * ph);
+      const T Qphi = ph - ph * ph * ph + o->lambda * U * (1.0 - ph * ph) * (1.0 - ph * ph);
       o->as2[i] = a2;
       for (int a = 0; a < 9; ++a) {
         const T he = heq(a, ph, Nx, Ny, d.Dphi);
@@ -375,7 +378,7 @@ void collide(Oracle<T>* o) {
       T q = 1.0 - ph;
       if (q < 0.0) q = T(0.0);
       if (q > 2.0) q = T(2.0);
-      const T tau_g = 3.0 * d.Dlat * q + 0.5;
+      const T tau_g = 3.0 * o->Dlat * q + 0.5;
       const T src = -0.5 * p.L_sat * (ph - o->phi_prev[i]);  // (dphi/dt) * dt
       for (int a = 0; a < 9; ++a) {
         const T ge = geq(a, U, usx, usy);
@@ -475,31 +478,42 @@ void step_once(Oracle<T>* o) {
 }
 
 // Initial populations: equilibria of the given moments (R13); phi^{-1} = phi^0 (R7).
+// rho, ux, uy may be empty (fluid at rest); without the flow lattice they are ignored.
 template <class T>
-void init_fields(Oracle<T>* o, const double* phi0, const double* U0, const double* rho0,
-                 const double* ux0, const double* uy0) {
-  std::vector<T> phi(o->n);
-  for (size_t i = 0; i < o->n; ++i) phi[i] = T(phi0[i]);
+void init_fields_t(Oracle<T>* o, const std::vector<T>& phi, const std::vector<T>& U,
+                   const std::vector<T>& rho0, const std::vector<T>& ux0,
+                   const std::vector<T>& uy0) {
   for (int y = 0; y < o->ny; ++y) {
     for (int x = 0; x < o->nx; ++x) {
       const size_t i = o->at(x, y);
       T gx, gy, as, Nx, Ny;
       gradient_at(*o, phi, x, y, &gx, &gy);
-      anisotropy(gx, gy, o->p.eps, o->p.kappa_N, &as, &Nx, &Ny);
+      anisotropy(gx, gy, o->eps, o->p.kappa_N, &as, &Nx, &Ny);
       // without the flow lattice the fluid is at rest (rho = 1, u = 0)
       const bool fl = o->p.flow != 0;
-      const T rho = (fl && rho0) ? T(rho0[i]) : T(1.0);
-      const T ux = (fl && ux0) ? T(ux0[i]) : T(0.0);
-      const T uy = (fl && uy0) ? T(uy0[i]) : T(0.0);
+      const T rho = (fl && !rho0.empty()) ? rho0[i] : T(1.0);
+      const T ux = (fl && !ux0.empty()) ? ux0[i] : T(0.0);
+      const T uy = (fl && !uy0.empty()) ? uy0[i] : T(0.0);
       for (int a = 0; a < 9; ++a) {
         o->h[a][i] = heq(a, phi[i], Nx, Ny, o->d.Dphi);
-        o->g[a][i] = geq(a, T(U0[i]), ux, uy);
+        o->g[a][i] = geq(a, U[i], ux, uy);
         if (o->p.flow) o->f[a][i] = feq(a, rho, ux, uy);
       }
     }
   }
   phi_field(*o, &o->phi_prev);
   o->steps = 0;
+}
+
+template <class T>
+void init_fields(Oracle<T>* o, const double* phi0, const double* U0, const double* rho0,
+                 const double* ux0, const double* uy0) {
+  auto vec = [&](const double* a) {
+    std::vector<T> v;
+    if (a) v.assign(a, a + o->n);
+    return v;
+  };
+  init_fields_t(o, vec(phi0), vec(U0), vec(rho0), vec(ux0), vec(uy0));
 }
 
 // Moments of the current state. which: 0 phi, 1 U, 2 rho, 3 u*_x, 4 u*_y, 5 phi history.
@@ -536,6 +550,72 @@ void get_field(const Oracle<T>& o, int which, double* out) {
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
+// Forward-mode dual numbers: a value and N directional derivatives, carried through the same
+// templated iteration as the double oracle, so a run yields the exact derivatives of the
+// discrete map (up to rounding) with respect to the seeded directions. The clamp of q (R8)
+// and the |grad phi| threshold (R4) are differentiated as the branch taken (zero slope
+// beyond the clamp, a_s = 1 below the threshold).
+// ---------------------------------------------------------------------------------------
+namespace {
+
+template <int N>
+struct Dual {
+  double v = 0.0;
+  double d[N] = {};
+  Dual() = default;
+  Dual(double x) : v(x) {}  // constants carry no derivative
+  explicit operator double() const { return v; }
+};
+
+template <int N> Dual<N> operator-(const Dual<N>& a) {
+  Dual<N> r(-a.v);
+  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <int N> Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r(a.v + b.v);
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <int N> Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r(a.v - b.v);
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+// product rule: (ab)' = a'b + ab'
+template <int N> Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r(a.v * b.v);
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+// quotient rule: (a/b)' = (a'b - ab') / b^2, written as (a' - (a/b) b') / b
+template <int N> Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r(a.v / b.v);
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+  return r;
+}
+template <int N> Dual<N> operator+(const Dual<N>& a, double b) { return a + Dual<N>(b); }
+template <int N> Dual<N> operator+(double a, const Dual<N>& b) { return Dual<N>(a) + b; }
+template <int N> Dual<N> operator-(const Dual<N>& a, double b) { return a - Dual<N>(b); }
+template <int N> Dual<N> operator-(double a, const Dual<N>& b) { return Dual<N>(a) - b; }
+template <int N> Dual<N> operator*(const Dual<N>& a, double b) { return a * Dual<N>(b); }
+template <int N> Dual<N> operator*(double a, const Dual<N>& b) { return Dual<N>(a) * b; }
+template <int N> Dual<N> operator/(const Dual<N>& a, double b) { return a / Dual<N>(b); }
+template <int N> Dual<N> operator/(double a, const Dual<N>& b) { return Dual<N>(a) / b; }
+template <int N> bool operator>(const Dual<N>& a, double b) { return a.v > b; }
+template <int N> bool operator<(const Dual<N>& a, double b) { return a.v < b; }
+// (sqrt s)' = s' / (2 sqrt s)
+template <int N> Dual<N> sqrt(const Dual<N>& a) {
+  Dual<N> r(std::sqrt(a.v));
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
+  return r;
+}
+
+using D4 = Dual<4>;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
 // C interface for the Python test harness (ctypes). Arrays are row-major [ny][nx] doubles;
 // population arrays are [9][ny][nx] in the D2Q9 order above. Errors return a negative code.
 // ---------------------------------------------------------------------------------------
@@ -551,6 +631,9 @@ void* orc_create(const orc_params* p) {
   if (!o) return nullptr;
   o->p = *p;
   o->d = d;
+  o->eps = p->eps;
+  o->Dlat = d.Dlat;
+  o->lambda = d.lambda;
   o->nx = p->nx;
   o->ny = p->ny;
   o->n = (size_t)p->nx * (size_t)p->ny;
@@ -650,6 +733,60 @@ int orc_gradient_periodic(const double* phi, int nx, int ny, double* gx, double*
 int orc_anisotropy(double gx, double gy, double eps, double kappa_N, double out[3]) {
   if (!out) return -1;
   anisotropy(gx, gy, eps, kappa_N, &out[0], &out[1], &out[2]);
+  return 0;
+}
+
+// Exact derivatives of the linear functional L = sum_x (wphi(x) phi_T(x) + wU(x) U_T(x)) of
+// the state after nsteps steps from the equilibrium state of the given moments (R13), with
+// respect to four directions: 0 eps; 1 D (through D_lat = D dt/dx^2 and, when lambda is not
+// given, through the beta = 0 lambda = tau0 D / (a2 W0^2) of Sec. 2.1); 2 lambda alone;
+// 3 the initial moments along (dphi, dU, drho, dux, duy). rho, ux, uy and their directions
+// may be null (fluid at rest). out = {L, dL/d0, dL/d1, dL/d2, dL/d3}.
+int orc_grad_run(const orc_params* p, const double* phi, const double* U, const double* rho,
+                 const double* ux, const double* uy, const double* dphi, const double* dU,
+                 const double* drho, const double* dux, const double* duy, int64_t nsteps,
+                 const double* wphi, const double* wU, double out[5]) {
+  if (!p || !phi || !U || !dphi || !dU || !wphi || !wU || !out || nsteps < 0) return -1;
+  Derived d;
+  if (!derive(*p, &d)) return -1;
+  Oracle<D4> o;
+  o.p = *p;
+  o.d = d;
+  o.nx = p->nx;
+  o.ny = p->ny;
+  o.n = (size_t)p->nx * (size_t)p->ny;
+  o.eps = D4(p->eps);
+  o.eps.d[0] = 1.0;
+  o.Dlat = D4(d.Dlat);
+  o.Dlat.d[1] = p->dt / (p->dx * p->dx);
+  o.lambda = D4(d.lambda);
+  o.lambda.d[2] = 1.0;
+  if (!(p->lambda > 0)) o.lambda.d[1] = p->tau0 / (kA2 * p->W0 * p->W0);
+  alloc(&o);
+  auto seeded = [&](const double* v, const double* dv) {
+    std::vector<D4> r;
+    if (!v) return r;
+    r.resize(o.n);
+    for (size_t i = 0; i < o.n; ++i) {
+      r[i] = D4(v[i]);
+      r[i].d[3] = dv ? dv[i] : 0.0;
+    }
+    return r;
+  };
+  init_fields_t(&o, seeded(phi, dphi), seeded(U, dU), seeded(rho, drho), seeded(ux, dux),
+                seeded(uy, duy));
+  for (int64_t s = 0; s < nsteps; ++s) step_once(&o);
+  D4 L(0.0);
+  D4 v[9];
+  for (size_t i = 0; i < o.n; ++i) {
+    for (int a = 0; a < 9; ++a) v[a] = o.h[a][i];
+    const D4 ph = sum9(v);
+    for (int a = 0; a < 9; ++a) v[a] = o.g[a][i];
+    const D4 Ui = sum9(v);
+    L = L + (wphi[i] * ph + wU[i] * Ui);
+  }
+  out[0] = L.v;
+  for (int k = 0; k < 4; ++k) out[1 + k] = L.d[k];
   return 0;
 }
 
