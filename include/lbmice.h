@@ -243,6 +243,49 @@ int lbmice_batch_set_shape(lbmice_batch_t* b, int32_t i, int32_t shape);
 /* Destroy the batch and all its members. Null is accepted. */
 int lbmice_batch_destroy(lbmice_batch_t* b);
 
+/* ---- gradients: checkpointed tape and the discrete adjoint of the step ----------------------
+ * Reverse-mode derivatives of a run with respect to the parameters eps, D and lambda and to
+ * the initial moment fields, for the loss L a caller builds from the final phi and U fields:
+ * the adjoint of every step (Sec. 2.2 collisions, Eq. (d) pull, E4 gradient of Sec. 3.1.1,
+ * anisotropy of Sec. 2.1) is hand-derived from the FP32 step and runs on the GPU.
+ * A tape records a grid that was initialised by lbmice_set_fields or lbmice_init_seed (an
+ * equilibrium state, step 0) and is then advanced only through lbmice_tape_record; it keeps
+ * the state every `every` steps (lbmice_state_bytes each, on the device). The reverse sweep
+ * restores each checkpoint, recomputes that segment's states and runs backwards through them
+ * (work space: every + 1 population buffers and every + 2 phi planes, allocated by the first
+ * backward). Supported: FP32 storage, periodic faces on all four sides (EINVAL otherwise).
+ * Non-differentiable points are taken as the branch the step takes: below the |grad phi|^2
+ * threshold the anisotropy does not depend on the gradient or on eps; q(phi) = 1 - phi has
+ * zero slope where its clamp to [0, 2] is active.                                             */
+typedef struct lbmice_tape lbmice_tape_t;
+
+/* Start a tape on grid h (borrowed; it must outlive the tape), keeping a checkpoint every
+ * `every` >= 1 steps. Errors: EINVAL (null, every < 1, h not at step 0, storage other than
+ * FP32, a face that is not periodic), ENOMEM, ECUDA. */
+int lbmice_tape_create(lbmice_t* h, int32_t every, lbmice_tape_t** out);
+
+/* Advance the grid by nsteps through lbmice_step, keeping checkpoints. Errors: EINVAL (the
+ * grid was stepped outside the tape), ENONFINITE (check_every), ENOMEM, ECUDA. */
+int lbmice_tape_record(lbmice_tape_t* t, int64_t nsteps);
+
+/* Steps recorded so far, -1 for a null tape. */
+int64_t lbmice_tape_steps(const lbmice_tape_t* t);
+
+/* Reverse sweep from the seeds phi_bar = dL/dphi_T and U_bar = dL/dU_T ([ny][nx] float32,
+ * host or device, either may be null = 0) at the recorded final step. grads (host, 3
+ * doubles, may be null) receives dL/d eps, dL/d D (through D dt/dx^2 and, when lambda is not
+ * given, through the beta = 0 lambda = tau0 D / (a2 W0^2) of Sec. 2.1) and dL/d lambda (lambda
+ * alone). phi0_bar, U0_bar, rho0_bar, ux0_bar, uy0_bar ([ny][nx] float32, host or device, each
+ * may be null) receive dL/d of the initial moment fields (rho0 and u0 are zero without the
+ * flow lattice). Synchronises the grid's stream. The tape may be swept again. Errors: EINVAL
+ * (the grid was stepped outside the tape), ENOMEM, ECUDA. */
+int lbmice_tape_backward(lbmice_tape_t* t, const float* phi_bar, const float* U_bar,
+                         double grads[3], float* phi0_bar, float* U0_bar, float* rho0_bar,
+                         float* ux0_bar, float* uy0_bar);
+
+/* Free the tape (checkpoints and work space); the grid is untouched. Null is accepted. */
+int lbmice_tape_destroy(lbmice_tape_t* t);
+
 /* ---- diagnostics without allocation -------------------------------------------------------
  * The paper has no counterpart: this is a service of the library, not a step of the method.
  * Some callers cannot allocate device memory when they want diagnostics -- for example an

@@ -74,7 +74,8 @@ def lib():
         L.orc_gradient_periodic.argtypes = [dp, i32, i32, dp, dp]
         L.orc_anisotropy.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, dp]
-        L.orc_grad_run.argtypes = [ctypes.POINTER(OrcParams)] + [dp] * 10 + [i64, dp, dp, dp]
+        L.orc_grad_run.argtypes = ([ctypes.POINTER(OrcParams)] + [dp] * 10 +
+                                   [i64, dp, dp, i32, dp, dp])
         _lib = L
     return _lib
 
@@ -190,11 +191,17 @@ def anisotropy(gx: float, gy: float, eps: float, kappa_N: float = 1.0):
 GRAD_KEYS = ("eps", "D", "lambda", "init")
 
 
-def grad_run(params: OrcParams, fields: dict, nsteps: int, wphi, wU, dfields: dict | None = None):
+def grad_run(params: OrcParams, fields: dict, nsteps: int, wphi, wU, dfields: dict | None = None,
+             round_f32: bool = False, along=None):
     """Exact forward-mode derivatives of L = sum(wphi * phi_T + wU * U_T) after ``nsteps``
     steps from the equilibrium state of ``fields`` (keys phi, U and optionally rho, ux, uy),
     with respect to eps, D (through D_lat and, if lambda is not given, the beta = 0 lambda),
     lambda alone, and the initial moments along ``dfields`` (same keys; missing = 0).
+    ``round_f32``: the state's values are rounded to float32 after every step (derivatives
+    kept), i.e. the derivatives along a float32-stored trajectory. ``along``: states to
+    differentiate along, shape (nsteps + 1, planes, ny, nx) -- the initial state and the
+    state after every step -- with planes h0..h8, g0..g8, [f0..f8,] phi, phi history; before
+    every step the state's values and the collision's phi values are replaced by them.
     Returns {"L": ..., "eps": ..., "D": ..., "lambda": ..., "init": ...}."""
     n = params.nx * params.ny
     dfields = dfields or {}
@@ -204,11 +211,17 @@ def grad_run(params: OrcParams, fields: dict, nsteps: int, wphi, wU, dfields: di
         v = dfields.get(k)
         df[k] = _f64(v) if v is not None else (np.zeros(n) if k in ("phi", "U") else None)
     w1, w2 = _f64(wphi), _f64(wU)
+    tr = None
+    if along is not None:
+        tr = _f64(along)
+        planes = (27 if params.flow else 18) + 2
+        if tr.shape != (nsteps + 1, planes, params.ny, params.nx):
+            raise ValueError("along must have shape (nsteps + 1, planes, ny, nx)")
     out = np.zeros(5)
     rc = lib().orc_grad_run(ctypes.byref(params), _dp(f["phi"]), _dp(f["U"]), _dp(f["rho"]),
                             _dp(f["ux"]), _dp(f["uy"]), _dp(df["phi"]), _dp(df["U"]),
                             _dp(df["rho"]), _dp(df["ux"]), _dp(df["uy"]), int(nsteps),
-                            _dp(w1), _dp(w2), _dp(out))
+                            _dp(w1), _dp(w2), 1 if round_f32 else 0, _dp(tr), _dp(out))
     if rc != 0:
         raise ValueError("oracle rejected the gradient run")
     return dict(zip(("L",) + GRAD_KEYS, out.tolist()))

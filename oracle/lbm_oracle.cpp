@@ -121,6 +121,9 @@ struct Oracle {
   // The parameters the gradient of the method is taken with respect to, in the scalar type
   // of the run (for T = double they are exactly p.eps, d.Dlat and d.lambda).
   T eps = T(0.0), Dlat = T(0.0), lambda = T(0.0);
+  // When set, the values (not the derivatives) of phi = sum h used by the next collision are
+  // taken from this [ny][nx] array: a gradient run differentiating along given states.
+  const double* phi_force = nullptr;
   int nx = 0, ny = 0;
   size_t n = 0;
   // Pre-collision populations at time t, one array per direction, node index y*nx + x.
@@ -338,12 +341,16 @@ namespace {
 // Collision of every node (the right-hand sides of the three LB equations of Sec. 2.2),
 // from the time-n state (R14). Fills fs, gs, hs (post-collision populations) and as2.
 // ---------------------------------------------------------------------------------------
+inline void set_value(double& x, double v) { x = v; }
+
 template <class T>
 void collide(Oracle<T>* o) {
   const orc_params& p = o->p;
   const Derived& d = o->d;
   std::vector<T> phi;
   phi_field(*o, &phi);
+  if (o->phi_force)
+    for (size_t i = 0; i < o->n; ++i) set_value(phi[i], o->phi_force[i]);
   for (int y = 0; y < o->ny; ++y) {
     for (int x = 0; x < o->nx; ++x) {
       const size_t i = o->at(x, y);
@@ -603,6 +610,7 @@ template <int N> Dual<N> operator*(double a, const Dual<N>& b) { return Dual<N>(
 template <int N> Dual<N> operator/(const Dual<N>& a, double b) { return a / Dual<N>(b); }
 template <int N> Dual<N> operator/(double a, const Dual<N>& b) { return Dual<N>(a) / b; }
 template <int N> bool operator>(const Dual<N>& a, double b) { return a.v > b; }
+template <int N> void set_value(Dual<N>& x, double v) { x.v = v; }
 template <int N> bool operator<(const Dual<N>& a, double b) { return a.v < b; }
 // (sqrt s)' = s' / (2 sqrt s)
 template <int N> Dual<N> sqrt(const Dual<N>& a) {
@@ -742,10 +750,20 @@ int orc_anisotropy(double gx, double gy, double eps, double kappa_N, double out[
 // given, through the beta = 0 lambda = tau0 D / (a2 W0^2) of Sec. 2.1); 2 lambda alone;
 // 3 the initial moments along (dphi, dU, drho, dux, duy). rho, ux, uy and their directions
 // may be null (fluid at rest). out = {L, dL/d0, dL/d1, dL/d2, dL/d3}.
+// round_f32 != 0: after every step the values (not the derivatives) of the populations and
+// of the phi history are rounded to float, so the derivatives are those along a trajectory
+// stored in float32 -- the spread against round_f32 = 0 measures how strongly the gradient
+// reacts to storage rounding.
+// along (may be null): states to differentiate along, nsteps + 1 blocks (the initial state,
+// then the state after every step), each holding the planes h0..h8, g0..g8, [f0..f8,] phi,
+// phi history, [ny][nx] each. The values (not the derivatives) of the state are replaced by
+// block s before step s + 1, and the collision of that step takes its phi values from the
+// block's phi plane, so the derivatives are those of the step linearised at the given states.
 int orc_grad_run(const orc_params* p, const double* phi, const double* U, const double* rho,
                  const double* ux, const double* uy, const double* dphi, const double* dU,
                  const double* drho, const double* dux, const double* duy, int64_t nsteps,
-                 const double* wphi, const double* wU, double out[5]) {
+                 const double* wphi, const double* wU, int32_t round_f32, const double* along,
+                 double out[5]) {
   if (!p || !phi || !U || !dphi || !dU || !wphi || !wU || !out || nsteps < 0) return -1;
   Derived d;
   if (!derive(*p, &d)) return -1;
@@ -775,7 +793,37 @@ int orc_grad_run(const orc_params* p, const double* phi, const double* U, const 
   };
   init_fields_t(&o, seeded(phi, dphi), seeded(U, dU), seeded(rho, drho), seeded(ux, dux),
                 seeded(uy, duy));
-  for (int64_t s = 0; s < nsteps; ++s) step_once(&o);
+  auto round_values = [](std::vector<D4>& v) {
+    for (D4& x : v) x.v = (double)(float)x.v;
+  };
+  const size_t nplanes = (p->flow ? 27 : 18) + 2;
+  auto force = [&](int64_t s) {  // values of block s; its phi plane for the next collision
+    const double* b = along + (size_t)s * nplanes * o.n;
+    auto put = [&](std::vector<D4>& v, const double* src) {
+      for (size_t i = 0; i < o.n; ++i) v[i].v = src[i];
+    };
+    for (int a = 0; a < 9; ++a) {
+      put(o.h[a], b + (size_t)a * o.n);
+      put(o.g[a], b + (size_t)(9 + a) * o.n);
+      if (o.p.flow) put(o.f[a], b + (size_t)(18 + a) * o.n);
+    }
+    put(o.phi_prev, b + (nplanes - 1) * o.n);
+    o.phi_force = b + (nplanes - 2) * o.n;
+  };
+  if (along) force(0);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    step_once(&o);
+    if (along) force(s + 1);
+    if (round_f32) {
+      for (int a = 0; a < 9; ++a) {
+        round_values(o.h[a]);
+        round_values(o.g[a]);
+        if (o.p.flow) round_values(o.f[a]);
+      }
+      round_values(o.phi_prev);
+    }
+  }
+  o.phi_force = nullptr;
   D4 L(0.0);
   D4 v[9];
   for (size_t i = 0; i < o.n; ++i) {

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/lbmice.h"
+#include "lbmice_adjoint.cuh"
 #include "lbmice_aux.cuh"
 #include "lbmice_step.cuh"
 
@@ -159,17 +160,8 @@ int with_storage(const lbmice_t* h, Fn&& fn) {
   }
 }
 
-int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
-  StepPtrs P;
-  P.pin = h->pops[s & 1];
-  P.pout = h->pops[(s + 1) & 1];
-  P.phi_n = h->phi[s % 3];
-  P.phi_nm1 = h->phi[(s + 2) % 3];
-  P.phi_np1 = h->phi[(s + 1) % 3];
-  P.U_n = h->Um[s & 1];
-  P.U_np1 = h->Um[(s + 1) & 1];
-  P.rho_n = h->rhom[s & 1];
-  P.rho_np1 = h->rhom[(s + 1) & 1];
+// One step of grid h on the given buffers.
+int launch_step_ptrs(const lbmice_t* h, const StepPtrs& P, cudaStream_t st) {
   const dim3 grd((h->C.nx + kTX - 1) / kTX, (h->C.ny + kTY - 1) / kTY), blk(kTX * kTY);
   return with_storage(h, [&](auto tag) {
     using S = decltype(tag);
@@ -181,6 +173,21 @@ int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
           <<<grd, blk, Tile<kTX, kTY>::smem_bytes<false>(), st>>>(h->C, P);
     return cuda_err(cudaGetLastError());
   });
+}
+
+// Step s of grid h on its own rotating buffers.
+int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
+  StepPtrs P;
+  P.pin = h->pops[s & 1];
+  P.pout = h->pops[(s + 1) & 1];
+  P.phi_n = h->phi[s % 3];
+  P.phi_nm1 = h->phi[(s + 2) % 3];
+  P.phi_np1 = h->phi[(s + 1) % 3];
+  P.U_n = h->Um[s & 1];
+  P.U_np1 = h->Um[(s + 1) & 1];
+  P.rho_n = h->rhom[s & 1];
+  P.rho_np1 = h->rhom[(s + 1) & 1];
+  return launch_step_ptrs(h, P, st);
 }
 
 int ensure_graph(lbmice_t* h) {
@@ -941,6 +948,292 @@ int lbmice_batch_destroy(lbmice_batch_t* b) {
   if (!b) return LBMICE_OK;
   cudaError_t e = cudaStreamSynchronize(b->stream);
   batch_release(b);
+  return cuda_err(e);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Tape: a checkpointed forward record of one grid and the discrete adjoint of its steps
+// (periodic faces, FP32 storage). Checkpoints are state blobs every `every` steps; the
+// reverse sweep restores each segment's checkpoint, recomputes the segment's states with the
+// step kernel and runs the adjoint kernels backwards through them.
+// ---------------------------------------------------------------------------------------
+struct lbmice_tape {
+  lbmice_t* h = nullptr;           // the recorded grid (borrowed)
+  int every = 100;                 // checkpoint interval
+  int64_t steps = 0;               // steps recorded
+  std::vector<void*> ckpt;         // states at steps 0, every, 2 every, ...
+  // reverse-sweep work space, allocated by the first backward
+  std::vector<float*> seg_pops;    // every + 1 population buffers: states of one segment
+  std::vector<float*> seg_phi;     // every + 2 phi planes: phi^{s0-1}, phi^{s0}, ...
+  float* pb[2] = {nullptr, nullptr};
+  float* Phib[2] = {nullptr, nullptr};
+  float* Psib[2] = {nullptr, nullptr};
+  std::vector<float*> plane;       // scratch planes, see enum below
+  double* partial = nullptr;       // [blocks][kAdjParams]
+  int nblocks = 0;
+};
+
+namespace {
+
+enum : int {
+  TP_PHIB_LOC = 0, TP_GBX, TP_GBY, TP_BN, TP_SEED_PHI, TP_SEED_U, TP_PHI0B, TP_U0B, TP_RHO0B,
+  TP_UX0B, TP_UY0B, TP_NPLANES
+};
+
+bool tape_supported(const lbmice_t* h) {
+  if (h->p.storage != LBMICE_STORAGE_F32) return false;
+  for (int f = 0; f < 4; ++f)
+    if (h->p.bc[f] != LBMICE_BC_PERIODIC) return false;
+  return true;
+}
+
+// State blob of the current step, kept when the step is a multiple of the interval.
+int tape_checkpoint(lbmice_tape_t* t) {
+  const size_t c = (size_t)(t->steps / t->every);
+  if (c < t->ckpt.size()) return LBMICE_OK;
+  void* blob = nullptr;
+  LB_TRY(cudaMalloc(&blob, lbmice_state_bytes(t->h)));
+  t->ckpt.push_back(blob);
+  return copy_state(t->h, blob, true, cudaMemcpyDeviceToDevice);
+}
+
+int tape_alloc_work(lbmice_tape_t* t) {
+  if (t->partial) return LBMICE_OK;
+  const lbmice_t* h = t->h;
+  auto grab = [](size_t bytes, float** p) { return cudaMalloc(reinterpret_cast<void**>(p), bytes); };
+  t->seg_pops.assign(t->every + 1, nullptr);
+  t->seg_phi.assign(t->every + 2, nullptr);
+  t->plane.assign(TP_NPLANES, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (float*& b : t->seg_pops) if (e == cudaSuccess) e = grab(pop_bytes(h), &b);
+  for (float*& b : t->seg_phi) if (e == cudaSuccess) e = grab(field_bytes(h), &b);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = grab(pop_bytes(h), &t->pb[k]);
+    if (e == cudaSuccess) e = grab(field_bytes(h), &t->Phib[k]);
+    if (e == cudaSuccess) e = grab(field_bytes(h), &t->Psib[k]);
+  }
+  for (float*& b : t->plane) if (e == cudaSuccess) e = grab(field_bytes(h), &b);
+  t->nblocks = ((h->C.nx + 31) / 32) * ((h->C.ny + 7) / 8);
+  if (e == cudaSuccess)
+    e = cudaMalloc(reinterpret_cast<void**>(&t->partial),
+                   sizeof(double) * kAdjParams * t->nblocks);
+  for (float* b : t->plane)  // planes are read over their full pitch by the copies out
+    if (e == cudaSuccess && b) e = cudaMemsetAsync(b, 0, field_bytes(h), h->stream);
+  return cuda_err(e);
+}
+
+void tape_free(lbmice_tape_t* t) {
+  for (void* b : t->ckpt) cudaFree(b);
+  for (float* b : t->seg_pops) if (b) cudaFree(b);
+  for (float* b : t->seg_phi) if (b) cudaFree(b);
+  for (int k = 0; k < 2; ++k) {
+    if (t->pb[k]) cudaFree(t->pb[k]);
+    if (t->Phib[k]) cudaFree(t->Phib[k]);
+    if (t->Psib[k]) cudaFree(t->Psib[k]);
+  }
+  for (float* b : t->plane) if (b) cudaFree(b);
+  if (t->partial) cudaFree(t->partial);
+  delete t;
+}
+
+// Checkpoint c into the first state of the segment buffers (blob: populations, phi^n,
+// phi^{n-1}, as copy_state writes it for FP32 storage).
+int tape_restore(lbmice_tape_t* t, size_t c) {
+  const lbmice_t* h = t->h;
+  const char* b = static_cast<const char*>(t->ckpt[c]);
+  LB_TRY(cudaMemcpyAsync(t->seg_pops[0], b, pop_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+  b += pop_bytes(h);
+  LB_TRY(cudaMemcpyAsync(t->seg_phi[1], b, field_bytes(h), cudaMemcpyDeviceToDevice,
+                         h->stream));
+  b += field_bytes(h);
+  LB_TRY(cudaMemcpyAsync(t->seg_phi[0], b, field_bytes(h), cudaMemcpyDeviceToDevice,
+                         h->stream));
+  return LBMICE_OK;
+}
+
+StepPtrs tape_step_ptrs(const lbmice_tape_t* t, int j) {
+  StepPtrs P{};
+  P.pin = t->seg_pops[j];
+  P.pout = t->seg_pops[j + 1];
+  P.phi_n = t->seg_phi[j + 1];
+  P.phi_nm1 = t->seg_phi[j];
+  P.phi_np1 = t->seg_phi[j + 2];
+  return P;
+}
+
+dim3 adj_grid(const lbmice_t* h) { return dim3((h->C.nx + 31) / 32, (h->C.ny + 7) / 8); }
+
+// Reverse step through segment state j: adjoint buffers cur -> 1 - cur.
+int tape_reverse_step(lbmice_tape_t* t, int j, int cur) {
+  const lbmice_t* h = t->h;
+  AdjPtrs A;
+  A.pops = t->seg_pops[j];
+  A.phi_n = t->seg_phi[j + 1];
+  A.phi_nm1 = t->seg_phi[j];
+  A.pb_in = t->pb[cur];
+  A.Phib_in = t->Phib[cur];
+  A.Psib_in = t->Psib[cur];
+  A.pb_out = t->pb[1 - cur];
+  A.Phib_out = t->Phib[1 - cur];
+  A.Psib_out = t->Psib[1 - cur];
+  A.phib_loc = t->plane[TP_PHIB_LOC];
+  A.gbx = t->plane[TP_GBX];
+  A.gby = t->plane[TP_GBY];
+  A.Bn = t->plane[TP_BN];
+  A.partial = t->partial;
+  const dim3 g = adj_grid(h);
+  if (h->p.flow)
+    adj_collide_kernel<true><<<g, 256, 0, h->stream>>>(h->C, A);
+  else
+    adj_collide_kernel<false><<<g, 256, 0, h->stream>>>(h->C, A);
+  adj_pull_kernel<<<g, 256, 0, h->stream>>>(h->C, A);
+  return cuda_err(cudaGetLastError());
+}
+
+// [ny][nx] float array (host or device) <-> [ny][pitch] plane.
+int plane_in(const lbmice_t* h, float* plane, const float* src) {
+  const size_t w = sizeof(float) * h->C.nx;
+  LB_TRY(cudaMemcpy2DAsync(plane, sizeof(float) * h->C.pitch, src, w, w, h->C.ny,
+                           cudaMemcpyDefault, h->stream));
+  return LBMICE_OK;
+}
+int plane_out(const lbmice_t* h, float* dst, const float* plane) {
+  const size_t w = sizeof(float) * h->C.nx;
+  LB_TRY(cudaMemcpy2DAsync(dst, w, plane, sizeof(float) * h->C.pitch, w, h->C.ny,
+                           cudaMemcpyDefault, h->stream));
+  return LBMICE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbmice_tape_create(lbmice_t* h, int32_t every, lbmice_tape_t** out) {
+  if (!out) return LBMICE_EINVAL;
+  *out = nullptr;
+  if (!h || every < 1 || !tape_supported(h) || h->step != 0) return LBMICE_EINVAL;
+  lbmice_tape_t* t = new (std::nothrow) lbmice_tape();
+  if (!t) return LBMICE_ENOMEM;
+  t->h = h;
+  t->every = every;
+  const int rc = tape_checkpoint(t);
+  if (rc != LBMICE_OK) {
+    tape_free(t);
+    return rc;
+  }
+  *out = t;
+  return LBMICE_OK;
+}
+
+int64_t lbmice_tape_steps(const lbmice_tape_t* t) { return t ? t->steps : -1; }
+
+int lbmice_tape_record(lbmice_tape_t* t, int64_t nsteps) {
+  if (!t || nsteps < 0) return LBMICE_EINVAL;
+  if (t->h->step != t->steps) return LBMICE_EINVAL;  // stepped outside the tape
+  int64_t left = nsteps;
+  while (left > 0) {
+    const int64_t chunk = std::min<int64_t>(left, t->every - t->steps % t->every);
+    const int rc = lbmice_step(t->h, chunk);
+    t->steps = t->h->step;
+    if (rc != LBMICE_OK) return rc;
+    left -= chunk;
+    if (t->steps % t->every == 0) {
+      const int rc2 = tape_checkpoint(t);
+      if (rc2 != LBMICE_OK) return rc2;
+    }
+  }
+  return LBMICE_OK;
+}
+
+int lbmice_tape_backward(lbmice_tape_t* t, const float* phi_bar, const float* U_bar,
+                         double grads[3], float* phi0_bar, float* U0_bar, float* rho0_bar,
+                         float* ux0_bar, float* uy0_bar) {
+  if (!t) return LBMICE_EINVAL;
+  lbmice_t* h = t->h;
+  if (h->step != t->steps) return LBMICE_EINVAL;
+  int rc = tape_alloc_work(t);
+  if (rc != LBMICE_OK) return rc;
+  const dim3 g = adj_grid(h);
+  // seed: dL/dphi_T into the phi-plane adjoint, dL/dU_T into the g adjoints
+  if (phi_bar && (rc = plane_in(h, t->plane[TP_SEED_PHI], phi_bar)) != LBMICE_OK) return rc;
+  if (U_bar && (rc = plane_in(h, t->plane[TP_SEED_U], U_bar)) != LBMICE_OK) return rc;
+  const float* sp = phi_bar ? t->plane[TP_SEED_PHI] : nullptr;
+  const float* su = U_bar ? t->plane[TP_SEED_U] : nullptr;
+  if (h->p.flow)
+    adj_seed_kernel<true><<<g, 256, 0, h->stream>>>(h->C, sp, su, t->pb[0], t->Phib[0],
+                                                    t->Psib[0]);
+  else
+    adj_seed_kernel<false><<<g, 256, 0, h->stream>>>(h->C, sp, su, t->pb[0], t->Phib[0],
+                                                     t->Psib[0]);
+  LB_TRY(cudaGetLastError());
+  LB_TRY(cudaMemsetAsync(t->partial, 0, sizeof(double) * kAdjParams * t->nblocks, h->stream));
+  int cur = 0;
+  // segments from the last: restore, recompute its states, reverse through them
+  const int64_t nseg = (t->steps + t->every - 1) / t->every;
+  for (int64_t c = nseg - 1; c >= 0; --c) {
+    const int64_t s0 = c * t->every;
+    const int len = (int)std::min<int64_t>(t->every, t->steps - s0);
+    if ((rc = tape_restore(t, (size_t)c)) != LBMICE_OK) return rc;
+    for (int j = 0; j + 1 < len; ++j)
+      if ((rc = launch_step_ptrs(h, tape_step_ptrs(t, j), h->stream)) != LBMICE_OK) return rc;
+    for (int j = len - 1; j >= 0; --j) {
+      if ((rc = tape_reverse_step(t, j, cur)) != LBMICE_OK) return rc;
+      cur = 1 - cur;
+    }
+  }
+  if (nseg == 0 && (rc = tape_restore(t, 0)) != LBMICE_OK) return rc;
+  // initial state: adjoints of the moments it was built from
+  InitAdjPtrs I;
+  I.pops = t->seg_pops[0];
+  I.phi0 = t->seg_phi[1];
+  I.pb = t->pb[cur];
+  I.Phib = t->Phib[cur];
+  I.Psib = t->Psib[cur];
+  I.phib_loc = t->plane[TP_PHIB_LOC];
+  I.gbx = t->plane[TP_GBX];
+  I.gby = t->plane[TP_GBY];
+  I.Ub = t->plane[TP_U0B];
+  I.rhob = t->plane[TP_RHO0B];
+  I.uxb = t->plane[TP_UX0B];
+  I.uyb = t->plane[TP_UY0B];
+  I.partial = t->partial;
+  if (h->p.flow)
+    adj_init_kernel<true><<<g, 256, 0, h->stream>>>(h->C, I);
+  else
+    adj_init_kernel<false><<<g, 256, 0, h->stream>>>(h->C, I);
+  adj_gather_kernel<<<g, 256, 0, h->stream>>>(h->C, t->plane[TP_PHIB_LOC], t->plane[TP_GBX],
+                                              t->plane[TP_GBY], t->plane[TP_PHI0B]);
+  LB_TRY(cudaGetLastError());
+  const float* outs[5] = {t->plane[TP_PHI0B], t->plane[TP_U0B], t->plane[TP_RHO0B],
+                          t->plane[TP_UX0B], t->plane[TP_UY0B]};
+  float* dsts[5] = {phi0_bar, U0_bar, rho0_bar, ux0_bar, uy0_bar};
+  for (int k = 0; k < 5; ++k)
+    if (dsts[k] && (rc = plane_out(h, dsts[k], outs[k])) != LBMICE_OK) return rc;
+  std::vector<double> part((size_t)kAdjParams * t->nblocks);
+  LB_TRY(cudaMemcpyAsync(part.data(), t->partial, sizeof(double) * part.size(),
+                         cudaMemcpyDeviceToHost, h->stream));
+  LB_TRY(cudaStreamSynchronize(h->stream));
+  double sum[kAdjParams] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = 0; b < t->nblocks; ++b)
+    for (int k = 0; k < kAdjParams; ++k) sum[k] += part[(size_t)b * kAdjParams + k];
+  if (grads) {
+    const lbmice_params& p = h->p;
+    // eps enters as eps and as kappa_N 6 eps; D as D_lat3 = 3 D dt/dx^2 and, when lambda is
+    // not given, through the beta = 0 lambda = tau0 D / (a2 W0^2) (Sec. 2.1)
+    grads[0] = sum[ADJ_EPS] + 6.0 * p.kappa_N * sum[ADJ_KN6EPS];
+    grads[1] = sum[ADJ_DLAT3] * 3.0 * p.dt / (p.dx * p.dx);
+    if (!(p.lambda > 0)) grads[1] += sum[ADJ_LAMBDA] * p.tau0 / (kA2 * p.W0 * p.W0);
+    grads[2] = sum[ADJ_LAMBDA];
+  }
+  return LBMICE_OK;
+}
+
+int lbmice_tape_destroy(lbmice_tape_t* t) {
+  if (!t) return LBMICE_OK;
+  const cudaError_t e = cudaStreamSynchronize(t->h->stream);
+  tape_free(t);
   return cuda_err(e);
 }
 

@@ -26,7 +26,9 @@ EXPORTS = ("lbmice_params_default", "lbmice_create", "lbmice_init_seed", "lbmice
            "lbmice_steps_done", "lbmice_destroy", "lbmice_strerror", "lbmice_state_bytes",
            "lbmice_stats_noalloc", "lbmice_batch_create", "lbmice_batch_size",
            "lbmice_batch_member", "lbmice_batch_step", "lbmice_batch_autotune",
-           "lbmice_batch_set_shape", "lbmice_batch_destroy", "lbmice_last_error")
+           "lbmice_batch_set_shape", "lbmice_batch_destroy", "lbmice_last_error",
+           "lbmice_tape_create", "lbmice_tape_record", "lbmice_tape_steps",
+           "lbmice_tape_backward", "lbmice_tape_destroy")
 
 
 class LbmiceError(RuntimeError):
@@ -88,6 +90,12 @@ def lib():
         L.lbmice_state_bytes.restype = sz
         L.lbmice_last_error.argtypes = []
         L.lbmice_last_error.restype = ctypes.c_char_p
+        L.lbmice_tape_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
+        L.lbmice_tape_record.argtypes = [vp, i64]
+        L.lbmice_tape_steps.argtypes = [vp]
+        L.lbmice_tape_steps.restype = i64
+        L.lbmice_tape_backward.argtypes = [vp, vp, vp, dp, vp, vp, vp, vp, vp]
+        L.lbmice_tape_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -356,6 +364,78 @@ class Batch:
             for m in self.members:
                 m.close()
             _check(lib().lbmice_batch_destroy(self._h), "lbmice_batch_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+GRAD_NAMES = ("eps", "D", "lambda")
+INIT_NAMES = ("phi0", "U0", "rho0", "ux0", "uy0")
+
+
+class Tape:
+    """Checkpointed record of a :class:`Lattice` and the discrete adjoint of its steps
+    (include/lbmice.h, lbmice_tape_*). The lattice must be freshly initialised (step 0) and
+    is advanced through :meth:`record` only."""
+
+    def __init__(self, lattice: Lattice, every: int = 100):
+        h = ctypes.c_void_p()
+        _check(lib().lbmice_tape_create(lattice.handle, int(every), ctypes.byref(h)),
+               "lbmice_tape_create")
+        self._h = h
+        self.lattice = lattice
+        self.every = int(every)
+
+    def record(self, n: int):
+        _check(lib().lbmice_tape_record(self._h, int(n)), "lbmice_tape_record")
+
+    @property
+    def steps(self) -> int:
+        return int(lib().lbmice_tape_steps(self._h))
+
+    def backward(self, phi_bar=None, U_bar=None):
+        """Reverse sweep from dL/dphi_T and dL/dU_T, (ny, nx) arrays: numpy (host results)
+        or CUDA tensors (device results). Returns ({eps, D, lambda}, {phi0, U0, rho0, ux0,
+        uy0}) with float32 fields of shape (ny, nx)."""
+        import torch
+        lat = self.lattice
+        shape = (lat.ny, lat.nx)
+        on_dev = any(isinstance(a, torch.Tensor) for a in (phi_bar, U_bar))
+        keep = []
+
+        def seed(a):
+            if a is None:
+                return None
+            if on_dev:
+                t = torch.as_tensor(a, device=lat.device).to(torch.float32).contiguous()
+                if tuple(t.shape) != shape:
+                    raise ValueError("seeds must have shape (ny, nx)")
+                keep.append(t)
+                return ctypes.c_void_p(t.data_ptr())
+            n = np.ascontiguousarray(a, dtype=np.float32)
+            if n.shape != shape:
+                raise ValueError("seeds must have shape (ny, nx)")
+            keep.append(n)
+            return _ptr_host(n)
+
+        sp, su = seed(phi_bar), seed(U_bar)
+        if on_dev:
+            outs = [torch.empty(shape, dtype=torch.float32, device=lat.device) for _ in INIT_NAMES]
+            ptrs = [ctypes.c_void_p(o.data_ptr()) for o in outs]
+        else:
+            outs = [np.empty(shape, dtype=np.float32) for _ in INIT_NAMES]
+            ptrs = [_ptr_host(o) for o in outs]
+        g = (ctypes.c_double * 3)()
+        _check(lib().lbmice_tape_backward(self._h, sp, su, g, *ptrs), "lbmice_tape_backward")
+        return dict(zip(GRAD_NAMES, list(g))), dict(zip(INIT_NAMES, outs))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().lbmice_tape_destroy(self._h), "lbmice_tape_destroy")
             self._h = None
 
     def __del__(self):

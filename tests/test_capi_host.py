@@ -93,6 +93,19 @@ def test_null_handles_are_rejected(L):
     assert L.lbmice_destroy(None) == 0
 
 
+def test_tape_rejects_null_arguments(L):
+    import ctypes
+    out = ctypes.c_void_p(1)
+    assert L.lbmice_tape_create(None, 10, ctypes.byref(out)) == lbmice.EINVAL
+    assert out.value is None  # *out is cleared on error
+    assert L.lbmice_tape_create(None, 10, None) == lbmice.EINVAL
+    assert L.lbmice_tape_record(None, 1) == lbmice.EINVAL
+    assert L.lbmice_tape_steps(None) == -1
+    assert L.lbmice_tape_backward(None, None, None, None, None, None, None, None,
+                                  None) == lbmice.EINVAL
+    assert L.lbmice_tape_destroy(None) == 0
+
+
 def test_lattice_refuses_to_run_without_cuda():
     import torch
     if torch.cuda.is_available():

@@ -99,3 +99,31 @@ def test_one_step_of_a_uniform_state(lam_given):
         assert g["D"] == 0.0
     else:
         assert g["D"] == pytest.approx(dlam * w.tau0 / (0.6267 * w.W0 ** 2), rel=1e-12)
+
+
+def test_differentiating_along_the_own_trajectory_changes_nothing():
+    # replacing the values by those the run produces itself must leave every derivative as is
+    w = small()
+    f = W.perturbed_fields(w, 6, amp_u=0.02)
+    rng = np.random.default_rng(7)
+    shape = (w.ny, w.nx)
+    wphi, wU = rng.uniform(-1, 1, shape), rng.uniform(-1, 1, shape)
+    dirs = {k: rng.uniform(-1, 1, shape) for k in f}
+    p = oracle.make_params(w.nx, w.ny, **w.params())
+    o = oracle.Oracle(p)
+    o.set_fields(**f)
+
+    def state():
+        return np.concatenate([o.pops(oracle.LAT_H), o.pops(oracle.LAT_G), o.pops(oracle.LAT_F),
+                               o.field(oracle.PHI)[None], o.field(oracle.PHI_PREV)[None]])
+
+    traj = [state()]
+    for _ in range(6):
+        o.step(1)
+        traj.append(state())
+    plain = oracle.grad_run(p, f, 6, wphi, wU, dirs)
+    along = oracle.grad_run(p, f, 6, wphi, wU, dirs, along=np.stack(traj))
+    assert plain == along
+    # and a different trajectory does change them (the option is not ignored)
+    moved = oracle.grad_run(p, f, 6, wphi, wU, dirs, along=np.stack(traj) * (1 + 1e-3))
+    assert moved["eps"] != plain["eps"]
