@@ -57,6 +57,10 @@ def parse():
                     help="steps of the 96-crystal batched sweep leg (0: skip)")
     ap.add_argument("--batch-count", type=int, default=96,
                     help="crystals of the batched sweep (profiling runs: the first n of the 96)")
+    ap.add_argument("--grad-steps", type=int, default=3000,
+                    help="steps of the gradient workload leg (512^2, adjoint; 0: skip)")
+    ap.add_argument("--grad-n", type=int, default=512,
+                    help="grid side of the gradient leg (profiling runs only)")
     return ap.parse_args()
 
 
@@ -284,6 +288,88 @@ def run_batched(args, stream, dist):
     return out
 
 
+# Bytes per node of one reverse step as built: the collision adjoint reads the state (27
+# populations, phi^n, phi^{n-1}) and the adjoint (27 + 2 planes) and writes 27 + 5 planes
+# (360 B); the pull adjoint reads 9 + 9 population planes and 6 planes, writes 9 + 1 (132 B);
+# recomputing the segment's forward states adds one step (228 B).
+REVERSE_BYTES_PER_NODE = 360 + 132 + 228
+
+
+def run_gradient(args, stream, dist):
+    """The gradient workload: 512^2 periodic, f + g + h, seed R = 6 at the centre, from
+    (U0, eps, D) = (0.3, 0.04, 2.0) towards the run of (0.4, 0.06, 2.5), checkpoints every
+    100 steps; L = sum (phi_T - phi_T^target)^2. Times the recorded forward and the reverse
+    sweep, and checks the gradient against central differences (h = 1e-3)."""
+    import torch
+    from paper_2101_07163_gb300 import lbmice
+    n, steps, every = args.grad_n, args.grad_steps, 100
+    w = W.Workload("grad", n, n, steps, flow=True, eps=0.04, D=2.0, U0=0.3, cx=n / 2,
+                   cy=n / 2, R0=6.0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def forward(U0, eps, D, tape=False):
+        lat = lbmice.Lattice(n, n, stream=stream, **dict(w.params(), eps=eps, D=D))
+        lat.init_seed(w.cx, w.cy, w.R0, U0)
+        t = lbmice.Tape(lat, every) if tape else None
+        return lat, t
+
+    def phi_T(U0, eps, D):
+        lat, _ = forward(U0, eps, D)
+        lat.step(steps)
+        out = torch.empty((n, n), dtype=torch.float32, device=dev)
+        lat.field(lbmice.PHI, out=out)
+        lat.sync()
+        lat.close()
+        return out.double()
+
+    target = phi_T(0.4, 0.06, 2.5)
+    lat, tape = forward(0.3, 0.04, 2.0, tape=True)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    barrier(dist)
+    e[0].record(stream)
+    tape.record(steps)
+    e[1].record(stream)
+    e[1].synchronize()
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    lat.field(lbmice.PHI, out=out)
+    lat.sync()
+    seed = (2.0 * (out.double() - target)).float().contiguous()
+    L0 = float(((out.double() - target) ** 2).sum())
+    tape.backward(seed)  # allocates the reverse work space
+    torch.cuda.synchronize()
+    e[2].record(stream)
+    grads, fields = tape.backward(seed)
+    e[3].record(stream)
+    e[3].synchronize()
+    fwd_ms = max_over_ranks(dist, e[0].elapsed_time(e[1]))
+    bwd_ms = max_over_ranks(dist, e[2].elapsed_time(e[3]))
+    g = {"U0": float(fields["U0"].double().sum()), "eps": grads["eps"], "D": grads["D"]}
+    tape.close()
+    lat.close()
+    h = 1e-3
+    base = {"U0": 0.3, "eps": 0.04, "D": 2.0}
+    fd, rel = {}, {}
+    for k, v in base.items():
+        up = float(((phi_T(**dict(base, **{k: v + h})) - target) ** 2).sum())
+        dn = float(((phi_T(**dict(base, **{k: v - h})) - target) ** 2).sum())
+        fd[k] = (up - dn) / (2 * h)
+        rel[k] = abs(g[k] - fd[k]) / abs(fd[k])
+    nodes = n * n
+    peak, _ = measured_peak()
+    ach = REVERSE_BYTES_PER_NODE * nodes * steps / (bwd_ms * 1e-3) / 1e9
+    return {"workload": "gradient %dx%d periodic f+g+h, %d steps, checkpoints every 100"
+                        % (n, n, steps),
+            "loss": L0, "gradient": g, "central_differences_h1e-3": fd, "rel_err_vs_fd": rel,
+            "forward_recorded_ms": fwd_ms, "reverse_ms": bwd_ms,
+            "reverse_mlups": nodes * steps / (bwd_ms * 1e-3) / 1e6,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "bytes_per_node_reverse_step":
+                             REVERSE_BYTES_PER_NODE,
+                         "kernels": "adj_collide_kernel + adj_pull_kernel + step_kernel "
+                                    "(segment recompute)"},
+            "gpu_launches_per_reverse_step": 3}
+
+
 def run_ours(args):
     import torch
     dist, rank, world = dist_init()
@@ -357,6 +443,9 @@ def run_ours(args):
     batched = None
     if args.batch_steps > 0:
         batched = run_batched(args, stream, dist)
+    gradient = None
+    if args.grad_steps > 0:
+        gradient = run_gradient(args, stream, dist)
 
     if rank != 0:
         for leg in legs.values():
@@ -418,6 +507,8 @@ def run_ours(args):
         batched["ms_per_step"] = batched.pop("ms") / batched["steps"]
         batched["unit"] = "MLUPS"
         line["batched"] = batched
+    if gradient is not None:
+        line["gradient"] = gradient
     if legs:
         out = {}
         for st, leg in legs.items():
