@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(const Consts C, const 
     const long long ip = (long long)y * R + x;  // population offset of the node
     const long long iq = (long long)y * PI + x;  // plane offset of the node
 
-    // ---- forward recomputation: exactly the step kernel's FP32 collision ----
+    // ---- forward recomputation of the node's collision (the step kernel's quantities, in
+    //      their unfactored form; values agree with the kernel's to rounding) ----
     float hv[9], gv[9], fv[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {

@@ -107,7 +107,7 @@ __device__ __forceinline__ void load9(const typename Storage<S>::T* __restrict__
   } else {
 #pragma unroll
     for (int a = 1; a < 9; ++a)
-      out[a] = (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f) * M + Storage<S>::load(base + a * pstride);
+      out[a] = fmaf(a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f, M, Storage<S>::load(base + a * pstride));
     out[0] =
         M - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
   }
@@ -123,7 +123,7 @@ __device__ __forceinline__ void store9(typename Storage<S>::T* __restrict__ base
   } else {
 #pragma unroll
     for (int a = 1; a < 9; ++a)
-      base[a * pstride] = Storage<S>::from_f(p[a] - (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f) * M);
+      base[a * pstride] = Storage<S>::from_f(fmaf(-(a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f), M, p[a]));
   }
 }
 

@@ -15,6 +15,8 @@
 // phi^{n+1} out; halo re-reads hit L2.
 #pragma once
 
+#include <type_traits>
+
 #include "../../include/lbmice.h"
 #include "lbmice_device.cuh"
 
@@ -43,6 +45,58 @@ struct Tile {
   template <bool FLOW>
   static constexpr size_t smem_bytes() {
     return sizeof(float) * (size_t)(PN + (FLOW ? 27 : 18) * SN + SN);
+  }
+};
+
+// Per-node coefficients of the three collisions, so that each direction costs a few FMAs:
+//   phase field, Eq. (d)/(e): h* = h - (h - h^eq)/eta + w Q dt/tau0, h^eq = w (phi - 3 Dphi
+//     c.N), stored divided by a_s^2:  h*/a_s^2 = a1 h + w (a2 - a3 c.N);
+//   vapour: g* = g - (g - g^eq)/tau_g + w S dt, g^eq = w U (1 + 3 c.u*):
+//     g* = b1 g + w (b2 + b3 c.u*);
+//   flow: BGK to the second-order f^eq(rho, u*) plus Guo forcing of F = -k u*:
+//     f* = c1 f + w (c2 + c.u* (c3 + c4 c.u*) + c.F (c5 + c6 c.u*)).
+// Every product and sum is an explicit fmaf or round-to-nearest operation: the compiler may
+// not contract them differently in different kernels, so every kernel that collides a node
+// (single-grid or batched) produces the same bits.
+template <bool FLOW>
+struct FactoredCollision {
+  float a1, a2, a3, b1, b2, b3, ux, uy;
+  float c1 = 0.0f, c2 = 0.0f, c3 = 0.0f, c4 = 0.0f, c5 = 0.0f, c6 = 0.0f, Fx = 0.0f, Fy = 0.0f;
+  __device__ __forceinline__ FactoredCollision(const Consts& C, float ph, float U, float rho,
+                                               float inv_as2, float inv_eta, float srcQ,
+                                               float inv_tg, float srcU, float k, float usx,
+                                               float usy)
+      : ux(usx), uy(usy) {
+    a1 = __fmul_rn(1.0f - inv_eta, inv_as2);
+    a2 = __fmul_rn(fmaf(ph, inv_eta, srcQ), inv_as2);
+    a3 = __fmul_rn(__fmul_rn(C.Dphi3, inv_eta), inv_as2);
+    b1 = 1.0f - inv_tg;
+    b2 = fmaf(U, inv_tg, srcU);
+    b3 = __fmul_rn(__fmul_rn(3.0f, U), inv_tg);
+    if (FLOW) {
+      Fx = -__fmul_rn(k, usx);
+      Fy = -__fmul_rn(k, usy);
+      const float uF = fmaf(usx, Fx, __fmul_rn(usy, Fy));
+      const float uu = fmaf(usx, usx, __fmul_rn(usy, usy));
+      const float r = __fmul_rn(rho, C.inv_tau_f);
+      c1 = 1.0f - C.inv_tau_f;
+      c2 = fmaf(r, fmaf(-1.5f, uu, 1.0f), -__fmul_rn(__fmul_rn(3.0f, C.guo), uF));
+      c3 = __fmul_rn(3.0f, r);
+      c4 = __fmul_rn(4.5f, r);
+      c5 = __fmul_rn(3.0f, C.guo);
+      c6 = __fmul_rn(9.0f, C.guo);
+    }
+  }
+  __device__ __forceinline__ float h(int a, float hv, float Nx, float Ny) const {
+    return fmaf(hv, a1, __fmul_rn(w_of(a), fmaf(-a3, cdot(a, Nx, Ny), a2)));
+  }
+  __device__ __forceinline__ float g(int a, float gv) const {
+    return fmaf(gv, b1, __fmul_rn(w_of(a), fmaf(b3, cdot(a, ux, uy), b2)));
+  }
+  __device__ __forceinline__ float f(int a, float fv) const {
+    const float cu = cdot(a, ux, uy);
+    const float t = fmaf(fmaf(c4, cu, c3), cu, c2);
+    return fmaf(fv, c1, __fmul_rn(w_of(a), fmaf(cdot(a, Fx, Fy), fmaf(c6, cu, c5), t)));
   }
 };
 
@@ -185,71 +239,35 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     for (int a = 0; a < 9; ++a) hown[a] = hv[a];
   }
   if constexpr (!Storage<S>::DEV) {
-    // FP32 storage: each collided population is formed and stored direction by direction
-    // (measured faster here than the factored form below)
+    // FP32 storage: the factored collision (FactoredCollision), each collided population
+    // stored as it is formed (no staging array: the kernel stays at 64 registers); the
+    // free-slip mirror is a uniform branch, so the common path stores at fixed
+    // shared-memory offsets
+    FactoredCollision<FLOW> fc(C, ph, U, rho, inv_as2, inv_eta, srcQ, inv_tg, srcU, k, usx, usy);
+    auto emit = [&](auto mirrored) {
+      constexpr bool M = decltype(mirrored)::value;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      int am = mirx ? mirx_of(a) : a;
-      am = miry ? miry_of(am) : am;
-      const float w = w_of(a);
-      // phase field, Eq. (d)/(e): h* = h - (h - h^eq)/eta + w Q dt/tau0; stored as h*/a_s^2
-      const float heq = w * (ph - C.Dphi3 * cdot(a, Nx, Ny));
-      const float hs = hv[a] - (hv[a] - heq) * inv_eta + w * srcQ;
-      spost[(PLANE_H + am) * T::SN + node] = hs * inv_as2;
-      // vapour: g* = g - (g - g^eq)/tau_g + w S dt, g^eq = w U (1 + 3 c.u*)
-      const float cu = cdot(a, usx, usy);
-      const float geq = w * U * (1.0f + 3.0f * cu);
-      spost[(PLANE_G + am) * T::SN + node] = gv[a] - (gv[a] - geq) * inv_tg + w * srcU;
-      if (FLOW) {
-        // flow: BGK to f^eq(rho, u*) plus Guo forcing of F = -k u*
-        const float Fx = -k * usx, Fy = -k * usy;
-        const float uF = usx * Fx + usy * Fy;
-        const float uu = usx * usx + usy * usy;
-        const float cF = cdot(a, Fx, Fy);
-        const float feq = w * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
-        const float force = C.guo * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
-        spost[(PLANE_F + am) * T::SN + node] = fv[a] - (fv[a] - feq) * C.inv_tau_f + force;
+      for (int a = 0; a < 9; ++a) {
+        int am = a;
+        if constexpr (M) {
+          am = mirx ? mirx_of(a) : a;
+          am = miry ? miry_of(am) : am;
+        }
+        spost[(PLANE_H + am) * T::SN + node] = fc.h(a, hv[a], Nx, Ny);
+        spost[(PLANE_G + am) * T::SN + node] = fc.g(a, gv[a]);
+        if (FLOW) spost[(PLANE_F + am) * T::SN + node] = fc.f(a, fv[a]);
       }
-    }
+    };
+    if (mirx || miry) emit(std::true_type{}); else emit(std::false_type{});
   } else {
-    // Per-node coefficients of the three collisions, so that each direction costs a few FMAs:
-    //   phase field, Eq. (d)/(e): h* = h - (h - h^eq)/eta + w Q dt/tau0, h^eq = w (phi - 3 Dphi
-    //     c.N), stored divided by a_s^2:  h*/a_s^2 = a1 h + w (a2 - a3 c.N);
-    //   vapour: g* = g - (g - g^eq)/tau_g + w S dt, g^eq = w U (1 + 3 c.u*):
-    //     g* = b1 g + w (b2 + b3 c.u*);
-    //   flow: BGK to the second-order f^eq(rho, u*) plus Guo forcing of F = -k u*:
-    //     f* = c1 f + w (c2 + c.u* (c3 + c4 c.u*) + c.F (c5 + c6 c.u*)).
-    const float a1 = (1.0f - inv_eta) * inv_as2;
-    const float a2 = (ph * inv_eta + srcQ) * inv_as2;
-    const float a3 = C.Dphi3 * inv_eta * inv_as2;
-    const float b1 = 1.0f - inv_tg;
-    const float b2 = U * inv_tg + srcU;
-    const float b3 = 3.0f * U * inv_tg;
-    float c1 = 0.0f, c2 = 0.0f, c3 = 0.0f, c4 = 0.0f, c5 = 0.0f, c6 = 0.0f, Fx = 0.0f, Fy = 0.0f;
-    if (FLOW) {
-      Fx = -k * usx;
-      Fy = -k * usy;
-      const float uF = usx * Fx + usy * Fy;
-      const float uu = usx * usx + usy * usy;
-      const float r = rho * C.inv_tau_f;
-      c1 = 1.0f - C.inv_tau_f;
-      c2 = r * (1.0f - 1.5f * uu) - 3.0f * C.guo * uF;
-      c3 = 3.0f * r;
-      c4 = 4.5f * r;
-      c5 = 3.0f * C.guo;
-      c6 = 9.0f * C.guo;
-    }
+    // 16-bit storage: the same factored collision, staged in registers, then stored
+    FactoredCollision<FLOW> fc(C, ph, U, rho, inv_as2, inv_eta, srcQ, inv_tg, srcU, k, usx, usy);
     float post[27];
   #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const float w = w_of(a);
-      const float cu = cdot(a, usx, usy);
-      post[PLANE_H + a] = fmaf(hv[a], a1, w * fmaf(-a3, cdot(a, Nx, Ny), a2));
-      post[PLANE_G + a] = fmaf(gv[a], b1, w * fmaf(b3, cu, b2));
-      if (FLOW) {
-        const float t = fmaf(fmaf(c4, cu, c3), cu, c2);
-        post[PLANE_F + a] = fmaf(fv[a], c1, w * fmaf(cdot(a, Fx, Fy), fmaf(c6, cu, c5), t));
-      }
+      post[PLANE_H + a] = fc.h(a, hv[a], Nx, Ny);
+      post[PLANE_G + a] = fc.g(a, gv[a]);
+      if (FLOW) post[PLANE_F + a] = fc.f(a, fv[a]);
     }
     constexpr int NQ = FLOW ? 27 : 18;
     if (!mirx && !miry) {
@@ -281,6 +299,15 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
   const int tx = tid % TX, ty = tid / TX;
 
   // ---- A: phi^n with a two-node halo ----
+  if (x0 >= 2 && y0 >= 2 && x0 + TX + 2 <= C.nx && y0 + TY + 2 <= C.ny) {
+    // the halo lies inside the grid (almost every tile): no ghost resolution
+    const float* __restrict__ pb = P.phi_n + (long long)(y0 - 2) * C.pitch + (x0 - 2);
+    const int pitch = (int)C.pitch;
+    for (int i = tid; i < T::PN; i += T::NT) {
+      const int lx = i % T::PW, ly = i / T::PW;
+      sphi[i] = __ldg(pb + ly * pitch + lx);
+    }
+  } else
   for (int i = tid; i < T::PN; i += T::NT) {
     const int lx = i % T::PW, ly = i / T::PW;
     const int X = x0 - 2 + lx, Y = y0 - 2 + ly;
@@ -358,8 +385,18 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
   }
 }
 
+// One CTA per TX x TY tile. FP32 storage is held to 64 registers (4 CTAs of 256 threads per
+// SM, the measured optimum); the 16-bit forms keep the compiler's own allocation, which a
+// minimum-blocks bound would change.
 template <int TX, int TY, bool FLOW, class S>
-__global__ void __launch_bounds__(TX* TY) step_kernel(const Consts C, const StepPtrs P) {
+__global__ std::enable_if_t<!Storage<S>::DEV> __launch_bounds__(TX* TY, 4)
+    step_kernel(const Consts C, const StepPtrs P) {
+  extern __shared__ float smem[];
+  step_tile<TX, TY, FLOW, S>(C, P, blockIdx.x * TX, blockIdx.y * TY, smem);
+}
+template <int TX, int TY, bool FLOW, class S>
+__global__ std::enable_if_t<Storage<S>::DEV> __launch_bounds__(TX* TY)
+    step_kernel(const Consts C, const StepPtrs P) {
   extern __shared__ float smem[];
   step_tile<TX, TY, FLOW, S>(C, P, blockIdx.x * TX, blockIdx.y * TY, smem);
 }

@@ -137,6 +137,38 @@ def test_mirror_symmetry_survives_16_bit_storage(storage):
         np.testing.assert_array_equal(a, a[iy, :])
 
 
+# ---- the plate physics at 2048 steps: max |dphi|, |dU| and the solid area ------------------
+
+@pytest.fixture(scope="module")
+def plate_2048():
+    from tests.test_parity_gpu import fp32_storage_floor
+    w = W.C3.with_size(160, 160)  # U0 = 0.5, eps = 0.05, D = 3, seed R0 = 10
+    f = W.seed_fields(w)
+    orc, floor = fp32_storage_floor(w, f, 2048)
+    return w, f, orc.field(oracle.PHI), orc.field(oracle.U), floor
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_plate_physics_2048_steps(storage, plate_2048):
+    # FP32 storage within 10x the spread of an FP32-stored oracle (as the parity tests);
+    # 16-bit storage within the 2000-step bounds of the 128^2 seed. Measured max |dphi|,
+    # |dU|: f32 4.1e-5, 1.8e-5 (floor 3.0e-5, 6.1e-6); f16 6.7e-5, 7.2e-5; bf16 2.4e-4, 3.3e-4.
+    w, f, ph, U, floor = plate_2048
+    lat = lbmice.Lattice(w.nx, w.ny, storage=storage, **w.params())
+    lat.set_fields(**f)
+    lat.step(2048)
+    p2, U2 = lat.field(lbmice.PHI), lat.field(lbmice.U)
+    if storage == "f32":
+        bphi, bU = max(10 * floor[oracle.PHI], 4e-6), max(10 * floor[oracle.U], 4e-6)
+    else:
+        bphi = bU = SEED_2000[storage]
+    assert maxdiff(p2, ph) < bphi
+    assert maxdiff(U2, U) < bU
+    area, aref = (0.5 * (1 + p2.astype(np.float64))).sum(), (0.5 * (1 + ph)).sum()
+    assert abs(area - aref) / aref < 1e-4
+
+
 # ---- long horizon: tip speed and solid area -----------------------------------------------
 
 LONG = W.C3.with_size(160, 160)  # the plate-regime physics (U0 = 0.5, eps = 0.05, D = 3)
