@@ -67,7 +67,8 @@ __global__ void equilibrium_kernel(const Consts C, double Dphi3, double eps, dou
   const double uy = uy0 ? uy0[i] : 0.0;
   const double uu = ux * ux + uy * uy;
   const long long o = (long long)Y * C.pitch + X;
-  typename ST::T* q0 = static_cast<typename ST::T*>(pops) + (long long)Y * C.rstride + X;
+  typename ST::T* pt = static_cast<typename ST::T*>(pops);
+  const long long nd = (long long)Y * C.rstride + X;
   float hv[9], gv[9], fv[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
@@ -80,13 +81,13 @@ __global__ void equilibrium_kernel(const Consts C, double Dphi3, double eps, dou
   const float s = sum9(hv);
   phi_cur[o] = s;
   phi_prev[o] = s;
-  store9<S>(q0 + PLANE_H * C.pstride, C.pstride, s, hv);
+  store9<S>(pt, 0, C.pstride, nd, s, hv);
   const float Ug = ST::DEV ? sum9(gv) : 0.0f;
-  store9<S>(q0 + PLANE_G * C.pstride, C.pstride, Ug, gv);
+  store9<S>(pt, 1, C.pstride, nd, Ug, gv);
   if (ST::DEV) U_cur[o] = Ug;
   if (FLOW) {
     const float rf = ST::DEV ? sum9(fv) : 0.0f;
-    store9<S>(q0 + PLANE_F * C.pstride, C.pstride, rf, fv);
+    store9<S>(pt, 2, C.pstride, nd, rf, fv);
     if (ST::DEV) rho_cur[o] = rf;
   }
 }
@@ -98,11 +99,10 @@ __device__ __forceinline__ void node_lattice(const Consts& C, const void* pops, 
                                              const float* rho, int X, int Y, float* out) {
   using ST = Storage<S>;
   const long long o = (long long)Y * C.pitch + X;
-  const typename ST::T* q0 =
-      static_cast<const typename ST::T*>(pops) + (long long)Y * C.rstride + X;
   float M = 0.0f;
   if (ST::DEV) M = L == 0 ? phi[o] : L == 1 ? U[o] : rho[o];
-  load9<S>(q0 + 9 * L * C.pstride, C.pstride, M, out);
+  load9<S>(static_cast<const typename ST::T*>(pops), L, C.pstride,
+           (long long)Y * C.rstride + X, M, out);
 }
 
 // One decoded population plane (lattice L, direction a) into a contiguous [ny][nx] array.
@@ -134,9 +134,8 @@ __global__ void encode_lattice_kernel(const Consts C, const float* __restrict__ 
   for (int a = 0; a < 9; ++a) v[a] = planes[a * n + i];
   const float m = sum9(v);
   if (M) M[(long long)Y * C.pitch + X] = m;
-  typename Storage<S>::T* q0 =
-      static_cast<typename Storage<S>::T*>(pops) + (long long)Y * C.rstride + X;
-  store9<S>(q0 + 9 * L * C.pstride, C.pstride, m, v);
+  store9<S>(static_cast<typename Storage<S>::T*>(pops), L, C.pstride,
+            (long long)Y * C.rstride + X, m, v);
 }
 
 // phi = sum h of the current populations (after a checkpoint load).

@@ -2,9 +2,10 @@
 // for sm_103a: the fused collide-stream kernel over the three D2Q9 lattices, the
 // equilibrium initialisation, the moment export and the FP64 reductions.
 //
-// State layout in HBM (one allocation per buffer, row pitch padded to 32 floats = 128 B):
+// State layout in HBM (one allocation per buffer, row pitch padded to 32 elements):
 //   populations: planes [h0..h8 | g0..g8 | f0..f8][ny][pitch] float, two buffers (the pull
-//                reads one and writes the other);
+//                reads one and writes the other); with 16-bit storage each lattice's region
+//                holds the 8 deviations of every node as one 16-byte vector (load9/store9);
 //   phi:         three rotating [ny][pitch] float planes holding phi^{n-1}, phi^n, phi^{n+1}
 //                (phi^n feeds the E4 gradient with a two-node halo, phi^{n-1} the d(phi)/dt
 //                of the vapour source, phi^{n+1} = sum h^{n+1} is written by the step).
@@ -69,7 +70,8 @@ __device__ __forceinline__ T sumcy9(const T* v) {
 // ---- storage of the populations ------------------------------------------------------
 // F32: the 9 populations of each lattice as float. F16 / BF16: the zeroth moment M of each
 // lattice as float (phi for h, U for g, rho for f, each in its own [ny][pitch] array) and the
-// 8 moving populations as 16-bit deviations d_a = p_a - w_a M; the rest population is rebuilt
+// 8 moving populations as 16-bit deviations d_a = p_a - w_a M (node-interleaved, below); the
+// rest population is rebuilt
 // as p_0 = M - sum_{a>0} p_a (summed in the pairing of sum9), so the populations sum back to
 // the stored M whatever the rounding of the deviations -- no systematic drift of mass or of
 // the vapour invariant. All arithmetic is FP32.
@@ -80,50 +82,97 @@ template <class S> struct Storage;
 template <> struct Storage<F32> {
   using T = float;
   static constexpr bool DEV = false;
-  __device__ static __forceinline__ float load(const T* p) { return __ldg(p); }
-  __device__ static __forceinline__ T from_f(float v) { return v; }
 };
+// 16-bit forms: the 8 deviations of one node and lattice are 16 contiguous bytes, moved by
+// one 128-bit load or store and converted in pairs (round to nearest).
 template <> struct Storage<F16> {
   using T = __half;
   static constexpr bool DEV = true;
-  __device__ static __forceinline__ float load(const T* p) { return __half2float(__ldg(p)); }
-  __device__ static __forceinline__ T from_f(float v) { return __float2half_rn(v); }
+  __device__ static __forceinline__ void unpack8(const uint4& v, float* d) {
+    const __half2* h = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __half22float2(h[k]);
+      d[2 * k] = f.x;
+      d[2 * k + 1] = f.y;
+    }
+  }
+  __device__ static __forceinline__ uint4 pack8(const float* d) {
+    uint4 v;
+    __half2* h = reinterpret_cast<__half2*>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2half2_rn(d[2 * k], d[2 * k + 1]);
+    return v;
+  }
 };
 template <> struct Storage<BF16> {
   using T = __nv_bfloat16;
   static constexpr bool DEV = true;
-  __device__ static __forceinline__ float load(const T* p) { return __bfloat162float(__ldg(p)); }
-  __device__ static __forceinline__ T from_f(float v) { return __float2bfloat16_rn(v); }
+  __device__ static __forceinline__ void unpack8(const uint4& v, float* d) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __bfloat1622float2(h[k]);
+      d[2 * k] = f.x;
+      d[2 * k + 1] = f.y;
+    }
+  }
+  __device__ static __forceinline__ uint4 pack8(const float* d) {
+    uint4 v;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(d[2 * k], d[2 * k + 1]);
+    return v;
+  }
 };
 
-// Populations of one lattice at node offset q0 (plane a at q0 + a * pstride): stored values
-// for F32, or rebuilt from the moment M and the deviations for F16 / BF16.
+// Addressing of the populations. Lattice L (0 h, 1 g, 2 f) owns 9 planes of pstride
+// elements, starting at element 9 L pstride of the buffer; node = y * rstride + x.
+//   F32: population a of the node at 9 L pstride + a pstride + node;
+//   F16 / BF16: the 8 deviations a = 1..8 of the node at 9 L pstride + 8 node + (a - 1)
+//     (16 bytes, 16-byte aligned because the pitch is a multiple of 32), the rest population
+//     not stored.
+
+// The 9 FP32 planes of one lattice at a node: base is the node's first population of the
+// lattice, planes pstride apart.
+__device__ __forceinline__ void load_planes9(const float* __restrict__ base, long long pstride,
+                                             float* out) {
+#pragma unroll
+  for (int a = 0; a < 9; ++a) out[a] = __ldg(base + a * pstride);
+}
+
+// Populations of lattice L at a node: stored values for F32, or rebuilt from the moment M
+// and the deviations for F16 / BF16.
 template <class S>
-__device__ __forceinline__ void load9(const typename Storage<S>::T* __restrict__ base,
-                                      long long pstride, float M, float* out) {
+__device__ __forceinline__ void load9(const typename Storage<S>::T* __restrict__ pops, int L,
+                                      long long pstride, long long node, float M, float* out) {
   if constexpr (!Storage<S>::DEV) {
-#pragma unroll
-    for (int a = 0; a < 9; ++a) out[a] = Storage<S>::load(base + a * pstride);
+    load_planes9(pops + node + 9 * L * pstride, pstride, out);
   } else {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(pops + 9 * L * pstride + 8 * node));
+    float d[8];
+    Storage<S>::unpack8(v, d);
 #pragma unroll
-    for (int a = 1; a < 9; ++a)
-      out[a] = fmaf(a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f, M, Storage<S>::load(base + a * pstride));
+    for (int a = 1; a < 9; ++a) out[a] = fmaf(a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f, M, d[a - 1]);
     out[0] =
         M - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
   }
 }
 
-// Store the 9 populations p of one lattice whose zeroth moment is M (= sum p).
+// Store the 9 populations p of lattice L at a node, whose zeroth moment is M (= sum p).
 template <class S>
-__device__ __forceinline__ void store9(typename Storage<S>::T* __restrict__ base,
-                                       long long pstride, float M, const float* p) {
+__device__ __forceinline__ void store9(typename Storage<S>::T* __restrict__ pops, int L,
+                                       long long pstride, long long node, float M,
+                                       const float* p) {
   if constexpr (!Storage<S>::DEV) {
+    float* __restrict__ n = pops + node;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) base[a * pstride] = Storage<S>::from_f(p[a]);
+    for (int a = 0; a < 9; ++a) n[(9 * L + a) * pstride] = p[a];
   } else {
+    float d[8];
 #pragma unroll
-    for (int a = 1; a < 9; ++a)
-      base[a * pstride] = Storage<S>::from_f(fmaf(-(a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f), M, p[a]));
+    for (int a = 1; a < 9; ++a) d[a - 1] = fmaf(-(a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f), M, p[a]);
+    *reinterpret_cast<uint4*>(pops + 9 * L * pstride + 8 * node) = Storage<S>::pack8(d);
   }
 }
 

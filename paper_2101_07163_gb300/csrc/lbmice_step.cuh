@@ -140,8 +140,9 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   }
   using ST = Storage<S>;
   const long long idx = (long long)my * C.pitch + mx;
-  const typename ST::T* __restrict__ pin =
-      static_cast<const typename ST::T*>(P.pin) + (long long)my * C.rstride + mx;
+  const typename ST::T* __restrict__ pops = static_cast<const typename ST::T*>(P.pin);
+  const long long nd = (long long)my * C.rstride + mx;
+  const typename ST::T* __restrict__ pin = pops + nd;  // FP32: the node's first population
 
   if (inlet >= 0) {
     // Inlet ghost: vapour at the inlet state, flow equilibrium at the adjacent density.
@@ -151,11 +152,11 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
                    : inlet == 2 ? C.uin_y[2] : C.uin_y[3];
     float rho = 1.0f;
     if (FLOW) {
-      if (ST::DEV) {
+      if constexpr (ST::DEV) {
         rho = __ldg(P.rho_n + idx);
       } else {
         float fv[9];
-        load9<S>(pin + PLANE_F * C.pstride, C.pstride, 0.0f, fv);
+        load_planes9(pin + PLANE_F * C.pstride, C.pstride, fv);  // FP32 only
         rho = sum9(fv);
       }
     }
@@ -177,10 +178,15 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   const int pc = (ly + 1) * T::PW + (lx + 1);
   const float ph = sphi[pc];
   float hv[9], gv[9], fv[9];
-  load9<S>(pin + PLANE_H * C.pstride, C.pstride, ph, hv);
-  load9<S>(pin + PLANE_G * C.pstride, C.pstride, ST::DEV ? __ldg(P.U_n + idx) : 0.0f, gv);
-  if (FLOW)
-    load9<S>(pin + PLANE_F * C.pstride, C.pstride, ST::DEV ? __ldg(P.rho_n + idx) : 0.0f, fv);
+  if constexpr (!ST::DEV) {
+    load_planes9(pin + PLANE_H * C.pstride, C.pstride, hv);
+    load_planes9(pin + PLANE_G * C.pstride, C.pstride, gv);
+    if (FLOW) load_planes9(pin + PLANE_F * C.pstride, C.pstride, fv);
+  } else {
+    load9<S>(pops, 0, C.pstride, nd, ph, hv);
+    load9<S>(pops, 1, C.pstride, nd, __ldg(P.U_n + idx), gv);
+    if (FLOW) load9<S>(pops, 2, C.pstride, nd, __ldg(P.rho_n + idx), fv);
+  }
   const float php = __ldg(P.phi_nm1 + idx);
   const float U = sum9(gv);
   float rho = 1.0f, jx = 0.0f, jy = 0.0f;
@@ -373,14 +379,16 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
     }
     const float phin = sum9(hn);
     P.phi_np1[idx] = phin;
-    store9<S>(out + PLANE_H * C.pstride, C.pstride, phin, hn);
+    typename ST::T* __restrict__ pout = static_cast<typename ST::T*>(P.pout);
+    const long long nd = (long long)Y * C.rstride + X;
+    store9<S>(pout, 0, C.pstride, nd, phin, hn);
     const float Un = sum9(gn);
     P.U_np1[idx] = Un;
-    store9<S>(out + PLANE_G * C.pstride, C.pstride, Un, gn);
+    store9<S>(pout, 1, C.pstride, nd, Un, gn);
     if (FLOW) {
       const float rn = sum9(fn);
       P.rho_np1[idx] = rn;
-      store9<S>(out + PLANE_F * C.pstride, C.pstride, rn, fn);
+      store9<S>(pout, 2, C.pstride, nd, rn, fn);
     }
   }
 }
