@@ -466,30 +466,21 @@ extern "C" int lbmice_fields(lbmice_t* h, int32_t which, void* dst, size_t bytes
   } else if (which == LBMICE_FIELD_POPS) {
     const size_t need = sizeof(float) * h->nplanes * nx * ny;
     if (bytes < need) return LBMICE_EINVAL;
-    if (!dev16(h)) {
-      const float* pops = static_cast<const float*>(h->pops[s & 1]);
-      for (int q = 0; q < h->nplanes; ++q)
-        LB_TRY(cudaMemcpy2DAsync(static_cast<float*>(dst) + (size_t)q * nx * ny,
-                                 nx * sizeof(float), pops + q * h->C.pstride,
-                                 h->C.rstride * sizeof(float), nx * sizeof(float), ny, kind,
-                                 h->stream));
-    } else {
-      // decode one plane at a time (into dst directly, or through the field buffer)
-      for (int q = 0; q < h->nplanes; ++q) {
-        float* out = dst_on_device ? static_cast<float*>(dst) + (size_t)q * nx * ny
-                                   : h->fieldbuf;
-        int rc = with_storage(h, [&](auto tag) {
-          using S = decltype(tag);
-          decode_plane_kernel<S><<<node_grid(h->C, blk), blk, 0, h->stream>>>(
-              h->C, h->pops[s & 1], q / 9, q % 9, h->phi[s % 3], h->Um[s & 1], h->rhom[s & 1],
-              out);
-          return cuda_err(cudaGetLastError());
-        });
-        if (rc != LBMICE_OK) return rc;
-        if (!dst_on_device)
-          LB_TRY(cudaMemcpyAsync(static_cast<float*>(dst) + (size_t)q * nx * ny, h->fieldbuf,
-                                 sizeof(float) * nx * ny, cudaMemcpyDeviceToHost, h->stream));
-      }
+    // decode one plane at a time (into dst directly, or through the field buffer)
+    for (int q = 0; q < h->nplanes; ++q) {
+      float* out = dst_on_device ? static_cast<float*>(dst) + (size_t)q * nx * ny
+                                 : h->fieldbuf;
+      int rc = with_storage(h, [&](auto tag) {
+        using S = decltype(tag);
+        decode_plane_kernel<S><<<node_grid(h->C, blk), blk, 0, h->stream>>>(
+            h->C, h->pops[s & 1], q / 9, q % 9, h->phi[s % 3], h->Um[s & 1], h->rhom[s & 1],
+            out);
+        return cuda_err(cudaGetLastError());
+      });
+      if (rc != LBMICE_OK) return rc;
+      if (!dst_on_device)
+        LB_TRY(cudaMemcpyAsync(static_cast<float*>(dst) + (size_t)q * nx * ny, h->fieldbuf,
+                               sizeof(float) * nx * ny, cudaMemcpyDeviceToHost, h->stream));
     }
   } else {
     const size_t need = sizeof(float) * nx * ny;
@@ -526,31 +517,21 @@ extern "C" int lbmice_load(lbmice_t* h, int32_t which, const void* src, size_t b
     if (rc != LBMICE_OK) return rc;
   } else if (which == LBMICE_FIELD_POPS) {
     if (bytes < sizeof(float) * h->nplanes * nx * ny) return LBMICE_EINVAL;
-    if (!dev16(h)) {
-      float* pops = static_cast<float*>(h->pops[s & 1]);
-      for (int q = 0; q < h->nplanes; ++q)
-        LB_TRY(cudaMemcpy2DAsync(pops + q * h->C.pstride, h->C.rstride * sizeof(float),
-                                 static_cast<const float*>(src) + (size_t)q * nx * ny,
-                                 nx * sizeof(float), nx * sizeof(float), ny, kind, h->stream));
-      phi_from_pops_kernel<<<node_grid(h->C, blk), blk, 0, h->stream>>>(h->C, pops,
-                                                                        h->phi[s % 3]);
-      LB_TRY(cudaGetLastError());
-    } else {
-      // stage the 9 float planes of each lattice in the free population buffer (it holds at
-      // least 9 nx ny floats), then encode them into the current one
-      float* stage = static_cast<float*>(h->pops[(s + 1) & 1]);
-      for (int L = 0; L < h->nplanes / 9; ++L) {
-        LB_TRY(cudaMemcpyAsync(stage, static_cast<const float*>(src) + (size_t)9 * L * nx * ny,
-                               sizeof(float) * 9 * nx * ny, kind, h->stream));
-        float* M = L == 0 ? h->phi[s % 3] : L == 1 ? h->Um[s & 1] : h->rhom[s & 1];
-        int rc = with_storage(h, [&](auto tag) {
-          using S = decltype(tag);
-          encode_lattice_kernel<S><<<node_grid(h->C, blk), blk, 0, h->stream>>>(
-              h->C, stage, L, h->pops[s & 1], M);
-          return cuda_err(cudaGetLastError());
-        });
-        if (rc != LBMICE_OK) return rc;
-      }
+    // stage the 9 float planes of each lattice in the free population buffer (it holds at
+    // least 9 nx ny floats), then encode them into the current one; the h lattice's moment
+    // is the phi^n plane, and with 16-bit storage U and rho are kept too
+    float* stage = static_cast<float*>(h->pops[(s + 1) & 1]);
+    for (int L = 0; L < h->nplanes / 9; ++L) {
+      LB_TRY(cudaMemcpyAsync(stage, static_cast<const float*>(src) + (size_t)9 * L * nx * ny,
+                             sizeof(float) * 9 * nx * ny, kind, h->stream));
+      float* M = L == 0 ? h->phi[s % 3] : L == 1 ? h->Um[s & 1] : h->rhom[s & 1];
+      int rc = with_storage(h, [&](auto tag) {
+        using S = decltype(tag);
+        encode_lattice_kernel<S><<<node_grid(h->C, blk), blk, 0, h->stream>>>(
+            h->C, stage, L, h->pops[s & 1], M);
+        return cuda_err(cudaGetLastError());
+      });
+      if (rc != LBMICE_OK) return rc;
     }
   } else {
     if (bytes < sizeof(float) * nx * ny) return LBMICE_EINVAL;
@@ -670,7 +651,7 @@ extern "C" int lbmice_stats_noalloc(const float* pops, const float* phi, const f
   C.pstride = (long long)pitch * ny;  // caller's layout: [plane][ny][pitch]
   C.rstride = pitch;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  stats_partial_kernel<F32><<<nblocks, kStatThreads, 0, st>>>(
+  stats_partial_kernel<F32P><<<nblocks, kStatThreads, 0, st>>>(
       C, flow, 0.5 * dx * dx, 0.5 * L_sat, pops, phi, phi_prev, nullptr, nullptr, partial);
   LB_TRY(cudaGetLastError());
   stats_final_kernel<<<1, 32, 0, st>>>(partial, nblocks, out);

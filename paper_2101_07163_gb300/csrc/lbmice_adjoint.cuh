@@ -24,8 +24,9 @@
 
 namespace lbmice {
 
-// Buffers of one reverse step. Populations and their adjoints use the forward strides
-// (q * pstride + y * rstride + x); every other plane is [ny][pitch].
+// Buffers of one reverse step. The forward populations are in the step's node-interleaved
+// FP32 layout (load_lattice_f32, f32_index); their adjoints are plain planes,
+// q * pstride + y * rstride + x; every other plane is [ny][pitch].
 struct AdjPtrs {
   const float* pops;     // forward state n: populations
   const float* phi_n;    // forward state n: the phi^n plane
@@ -88,11 +89,13 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(const Consts C, const 
     // ---- forward recomputation of the node's collision (the step kernel's quantities, in
     //      their unfactored form; values agree with the kernel's to rounding) ----
     float hv[9], gv[9], fv[9];
+    load_lattice_f32(A.pops + PLANE_H * Q, Q, ip, hv);
+    load_lattice_f32(A.pops + PLANE_G * Q, Q, ip, gv);
+    if (FLOW) {
+      load_lattice_f32(A.pops + PLANE_F * Q, Q, ip, fv);
+    } else {
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      hv[a] = __ldg(A.pops + (PLANE_H + a) * Q + ip);
-      gv[a] = __ldg(A.pops + (PLANE_G + a) * Q + ip);
-      fv[a] = FLOW ? __ldg(A.pops + (PLANE_F + a) * Q + ip) : 0.0f;
+      for (int a = 0; a < 9; ++a) fv[a] = 0.0f;
     }
     const float ph = __ldg(A.phi_n + iq);
     const float U = sum9(gv);
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(const Consts C, const 
       const float hhat = __ldg(A.pb_in + (PLANE_H + a) * Q + jp) +
                          __ldg(A.Phib_in + (long long)ys * PI + xs);
       Ab[a] = hhat;
-      Bb += hhat * __ldg(A.pops + (PLANE_H + a) * Q + jp);
+      Bb += hhat * __ldg(A.pops + PLANE_H * Q + f32_index(Q, jp, a));
       Gb[a] = __ldg(A.pb_in + (PLANE_G + a) * Q + jp);
       Fb[a] = FLOW ? __ldg(A.pb_in + (PLANE_F + a) * Q + jp) : 0.0f;
     }
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const Consts C, const Adj
 // plane, U0 = sum g, rho0 = sum f, u0 = (sum c f) / rho0. Writes the node-local phi0 adjoint
 // (phib_loc), the adjoint of grad phi0 (gbx, gby) and the adjoints of U0, rho0, u0.
 struct InitAdjPtrs {
-  const float* pops;     // state 0
+  const float* pops;     // state 0 (node-interleaved FP32 layout)
   const float* phi0;     // phi plane of state 0
   const float* pb;       // adjoint of the state-0 populations
   const float* Phib;     // adjoint of the state-0 phi plane
@@ -379,10 +382,15 @@ __global__ void __launch_bounds__(256) adj_init_kernel(const Consts C, const Ini
     const float gy = kW1 * (P(x, yp) - P(x, ym)) + kW2 * ((P(xp, yp) - P(xp, ym)) +
                                                           (P(xm, yp) - P(xm, ym)));
     float gv[9], fv[9], hb[9], gbv[9], fbv[9];
+    load_lattice_f32(A.pops + PLANE_G * Q, Q, ip, gv);
+    if (FLOW) {
+      load_lattice_f32(A.pops + PLANE_F * Q, Q, ip, fv);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) fv[a] = 0.0f;
+    }
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      gv[a] = __ldg(A.pops + (PLANE_G + a) * Q + ip);
-      fv[a] = FLOW ? __ldg(A.pops + (PLANE_F + a) * Q + ip) : 0.0f;
       hb[a] = __ldg(A.pb + (PLANE_H + a) * Q + ip);
       gbv[a] = __ldg(A.pb + (PLANE_G + a) * Q + ip);
       fbv[a] = FLOW ? __ldg(A.pb + (PLANE_F + a) * Q + ip) : 0.0f;

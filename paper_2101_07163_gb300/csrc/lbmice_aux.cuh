@@ -138,20 +138,6 @@ __global__ void encode_lattice_kernel(const Consts C, const float* __restrict__ 
             (long long)Y * C.rstride + X, m, v);
 }
 
-// phi = sum h of the current populations (after a checkpoint load).
-__global__ void phi_from_pops_kernel(const Consts C, const float* __restrict__ pops,
-                                     float* __restrict__ phi) {
-  const int X = blockIdx.x * blockDim.x + threadIdx.x;
-  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (X >= C.nx || Y >= C.ny) return;
-  const long long o = (long long)Y * C.pitch + X;
-  const long long q0 = (long long)Y * C.rstride + X;
-  float hv[9];
-#pragma unroll
-  for (int a = 0; a < 9; ++a) hv[a] = pops[(PLANE_H + a) * C.pstride + q0];
-  phi[o] = sum9(hv);
-}
-
 // Moment of the current state into a contiguous [ny][nx] float array.
 // which: 0 phi, 1 U, 2 rho, 3 u*_x, 4 u*_y, 5 phi history.
 template <class S>

@@ -3,9 +3,11 @@
 // equilibrium initialisation, the moment export and the FP64 reductions.
 //
 // State layout in HBM (one allocation per buffer, row pitch padded to 32 elements):
-//   populations: planes [h0..h8 | g0..g8 | f0..f8][ny][pitch] float, two buffers (the pull
-//                reads one and writes the other); with 16-bit storage each lattice's region
-//                holds the 8 deviations of every node as one 16-byte vector (load9/store9);
+//   populations: three lattice regions [h | g | f], each 9 [ny][pitch] planes long, two
+//                buffers (the pull reads one and writes the other). Within a region the
+//                populations are node-interleaved (load9/store9 below): FP32 keeps directions
+//                1..4 and 5..8 of a node as two float4 and the rest population as a float;
+//                16-bit storage keeps the 8 deviations of a node as one 16-byte vector;
 //   phi:         three rotating [ny][pitch] float planes holding phi^{n-1}, phi^n, phi^{n+1}
 //                (phi^n feeds the E4 gradient with a two-node halo, phi^{n-1} the d(phi)/dt
 //                of the vapour source, phi^{n+1} = sum h^{n+1} is written by the step).
@@ -78,16 +80,24 @@ __device__ __forceinline__ T sumcy9(const T* v) {
 struct F32 {};
 struct F16 {};
 struct BF16 {};
+struct F32P {};  // FP32 populations in the exported plane layout (caller-owned diagnostics)
 template <class S> struct Storage;
 template <> struct Storage<F32> {
   using T = float;
   static constexpr bool DEV = false;
+  static constexpr bool PLANES = false;
+};
+template <> struct Storage<F32P> {
+  using T = float;
+  static constexpr bool DEV = false;
+  static constexpr bool PLANES = true;
 };
 // 16-bit forms: the 8 deviations of one node and lattice are 16 contiguous bytes, moved by
 // one 128-bit load or store and converted in pairs (round to nearest).
 template <> struct Storage<F16> {
   using T = __half;
   static constexpr bool DEV = true;
+  static constexpr bool PLANES = false;
   __device__ static __forceinline__ void unpack8(const uint4& v, float* d) {
     const __half2* h = reinterpret_cast<const __half2*>(&v);
 #pragma unroll
@@ -108,6 +118,7 @@ template <> struct Storage<F16> {
 template <> struct Storage<BF16> {
   using T = __nv_bfloat16;
   static constexpr bool DEV = true;
+  static constexpr bool PLANES = false;
   __device__ static __forceinline__ void unpack8(const uint4& v, float* d) {
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
 #pragma unroll
@@ -127,18 +138,41 @@ template <> struct Storage<BF16> {
 };
 
 // Addressing of the populations. Lattice L (0 h, 1 g, 2 f) owns 9 planes of pstride
-// elements, starting at element 9 L pstride of the buffer; node = y * rstride + x.
-//   F32: population a of the node at 9 L pstride + a pstride + node;
-//   F16 / BF16: the 8 deviations a = 1..8 of the node at 9 L pstride + 8 node + (a - 1)
-//     (16 bytes, 16-byte aligned because the pitch is a multiple of 32), the rest population
-//     not stored.
+// elements, starting at element 9 L pstride of the buffer; node = y * rstride + x. Within it:
+//   F32: directions 1..4 of the node as one float4 at element 4 node, directions 5..8 as one
+//     float4 at 4 pstride + 4 node, the rest population at 8 pstride + node;
+//   F16 / BF16: the 8 deviations a = 1..8 of the node at 8 node + (a - 1), the rest population
+//     not stored;
+//   F32P (diagnostics of caller-owned exports only): population a at a pstride + node.
+// Every vector is 16-byte aligned because the pitch is a multiple of 32 elements; a warp's 32
+// nodes move as 512 contiguous bytes per vector.
 
-// The 9 FP32 planes of one lattice at a node: base is the node's first population of the
-// lattice, planes pstride apart.
-__device__ __forceinline__ void load_planes9(const float* __restrict__ base, long long pstride,
-                                             float* out) {
-#pragma unroll
-  for (int a = 0; a < 9; ++a) out[a] = __ldg(base + a * pstride);
+// Index of population a of a node within an FP32 lattice region.
+__device__ __forceinline__ long long f32_index(long long pstride, long long node, int a) {
+  return a == 0 ? 8 * pstride + node
+                : (a < 5 ? 4 * node + (a - 1) : 4 * pstride + 4 * node + (a - 5));
+}
+
+// The 9 FP32 populations of one lattice region at a node.
+__device__ __forceinline__ void load_lattice_f32(const float* __restrict__ lat, long long pstride,
+                                                 long long node, float* out) {
+  const float4 p = __ldg(reinterpret_cast<const float4*>(lat + 4 * node));
+  const float4 q = __ldg(reinterpret_cast<const float4*>(lat + 4 * pstride + 4 * node));
+  out[0] = __ldg(lat + 8 * pstride + node);
+  out[1] = p.x;
+  out[2] = p.y;
+  out[3] = p.z;
+  out[4] = p.w;
+  out[5] = q.x;
+  out[6] = q.y;
+  out[7] = q.z;
+  out[8] = q.w;
+}
+__device__ __forceinline__ void store_lattice_f32(float* __restrict__ lat, long long pstride,
+                                                  long long node, const float* v) {
+  *reinterpret_cast<float4*>(lat + 4 * node) = make_float4(v[1], v[2], v[3], v[4]);
+  *reinterpret_cast<float4*>(lat + 4 * pstride + 4 * node) = make_float4(v[5], v[6], v[7], v[8]);
+  lat[8 * pstride + node] = v[0];
 }
 
 // Populations of lattice L at a node: stored values for F32, or rebuilt from the moment M
@@ -146,8 +180,11 @@ __device__ __forceinline__ void load_planes9(const float* __restrict__ base, lon
 template <class S>
 __device__ __forceinline__ void load9(const typename Storage<S>::T* __restrict__ pops, int L,
                                       long long pstride, long long node, float M, float* out) {
-  if constexpr (!Storage<S>::DEV) {
-    load_planes9(pops + node + 9 * L * pstride, pstride, out);
+  if constexpr (Storage<S>::PLANES) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) out[a] = __ldg(pops + (9 * L + a) * pstride + node);
+  } else if constexpr (!Storage<S>::DEV) {
+    load_lattice_f32(pops + 9 * L * pstride, pstride, node, out);
   } else {
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(pops + 9 * L * pstride + 8 * node));
     float d[8];
@@ -164,10 +201,11 @@ template <class S>
 __device__ __forceinline__ void store9(typename Storage<S>::T* __restrict__ pops, int L,
                                        long long pstride, long long node, float M,
                                        const float* p) {
-  if constexpr (!Storage<S>::DEV) {
-    float* __restrict__ n = pops + node;
+  if constexpr (Storage<S>::PLANES) {
 #pragma unroll
-    for (int a = 0; a < 9; ++a) n[(9 * L + a) * pstride] = p[a];
+    for (int a = 0; a < 9; ++a) pops[(9 * L + a) * pstride + node] = p[a];
+  } else if constexpr (!Storage<S>::DEV) {
+    store_lattice_f32(pops + 9 * L * pstride, pstride, node, p);
   } else {
     float d[8];
 #pragma unroll

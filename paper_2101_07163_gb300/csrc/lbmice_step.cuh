@@ -142,7 +142,6 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   const long long idx = (long long)my * C.pitch + mx;
   const typename ST::T* __restrict__ pops = static_cast<const typename ST::T*>(P.pin);
   const long long nd = (long long)my * C.rstride + mx;
-  const typename ST::T* __restrict__ pin = pops + nd;  // FP32: the node's first population
 
   if (inlet >= 0) {
     // Inlet ghost: vapour at the inlet state, flow equilibrium at the adjacent density.
@@ -156,7 +155,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
         rho = __ldg(P.rho_n + idx);
       } else {
         float fv[9];
-        load_planes9(pin + PLANE_F * C.pstride, C.pstride, fv);  // FP32 only
+        load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, fv);
         rho = sum9(fv);
       }
     }
@@ -179,9 +178,9 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   const float ph = sphi[pc];
   float hv[9], gv[9], fv[9];
   if constexpr (!ST::DEV) {
-    load_planes9(pin + PLANE_H * C.pstride, C.pstride, hv);
-    load_planes9(pin + PLANE_G * C.pstride, C.pstride, gv);
-    if (FLOW) load_planes9(pin + PLANE_F * C.pstride, C.pstride, fv);
+    load_lattice_f32(pops + PLANE_H * C.pstride, C.pstride, nd, hv);
+    load_lattice_f32(pops + PLANE_G * C.pstride, C.pstride, nd, gv);
+    if (FLOW) load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, fv);
   } else {
     load9<S>(pops, 0, C.pstride, nd, ph, hv);
     load9<S>(pops, 1, C.pstride, nd, __ldg(P.U_n + idx), gv);
@@ -352,19 +351,22 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
   const int X = x0 + tx, Y = y0 + ty;
   if (X >= C.nx || Y >= C.ny) return;  // (this thread has no node in this tile)
   const long long idx = (long long)Y * C.pitch + X;
-  typename ST::T* __restrict__ out =
-      static_cast<typename ST::T*>(P.pout) + (long long)Y * C.rstride + X;
   float hn[9];
   if constexpr (!ST::DEV) {
-    // FP32 storage: each pulled population goes straight back to HBM
+    // FP32 storage: each lattice's pulled populations go back as two float4 and a float
+    float gn[9], fn[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const int src = (ty + 1 - cy_of(a)) * T::SW + (tx + 1 - cx_of(a));
       hn[a] = fmaf(hown[a], sB[src], spost[(PLANE_H + a) * T::SN + src]);
-      out[(PLANE_H + a) * C.pstride] = hn[a];
-      out[(PLANE_G + a) * C.pstride] = spost[(PLANE_G + a) * T::SN + src];
-      if (FLOW) out[(PLANE_F + a) * C.pstride] = spost[(PLANE_F + a) * T::SN + src];
+      gn[a] = spost[(PLANE_G + a) * T::SN + src];
+      if (FLOW) fn[a] = spost[(PLANE_F + a) * T::SN + src];
     }
+    float* __restrict__ po = static_cast<float*>(P.pout);
+    const long long nd = (long long)Y * C.rstride + X;
+    store_lattice_f32(po + PLANE_H * C.pstride, C.pstride, nd, hn);
+    store_lattice_f32(po + PLANE_G * C.pstride, C.pstride, nd, gn);
+    if (FLOW) store_lattice_f32(po + PLANE_F * C.pstride, C.pstride, nd, fn);
     P.phi_np1[idx] = sum9(hn);
   } else {
     // 16-bit storage: the moments of the pulled populations are stored in FP32 and the
