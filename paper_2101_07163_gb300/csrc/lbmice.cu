@@ -954,6 +954,9 @@ struct lbmice_tape {
   std::vector<float*> plane;       // scratch planes, see enum below
   double* partial = nullptr;       // [blocks][kAdjParams]
   int nblocks = 0;
+  // a full segment's recompute and reverse steps as a CUDA graph, one per starting parity of
+  // the adjoint ping-pong (every argument is the same for every full segment)
+  cudaGraphExec_t seg_graph[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -1006,6 +1009,7 @@ int tape_alloc_work(lbmice_tape_t* t) {
 }
 
 void tape_free(lbmice_tape_t* t) {
+  for (cudaGraphExec_t g : t->seg_graph) if (g) cudaGraphExecDestroy(g);
   for (void* b : t->ckpt) cudaFree(b);
   for (float* b : t->seg_pops) if (b) cudaFree(b);
   for (float* b : t->seg_phi) if (b) cudaFree(b);
@@ -1047,7 +1051,7 @@ StepPtrs tape_step_ptrs(const lbmice_tape_t* t, int j) {
 dim3 adj_grid(const lbmice_t* h) { return dim3((h->C.nx + 31) / 32, (h->C.ny + 7) / 8); }
 
 // Reverse step through segment state j: adjoint buffers cur -> 1 - cur.
-int tape_reverse_step(lbmice_tape_t* t, int j, int cur) {
+int tape_reverse_step(lbmice_tape_t* t, int j, int cur, cudaStream_t st) {
   const lbmice_t* h = t->h;
   AdjPtrs A;
   A.pops = t->seg_pops[j];
@@ -1066,11 +1070,24 @@ int tape_reverse_step(lbmice_tape_t* t, int j, int cur) {
   A.partial = t->partial;
   const dim3 g = adj_grid(h);
   if (h->p.flow)
-    adj_collide_kernel<true><<<g, 256, 0, h->stream>>>(h->C, A);
+    adj_collide_kernel<true><<<g, 256, 0, st>>>(h->C, A);
   else
-    adj_collide_kernel<false><<<g, 256, 0, h->stream>>>(h->C, A);
-  adj_pull_kernel<<<g, 256, 0, h->stream>>>(h->C, A);
+    adj_collide_kernel<false><<<g, 256, 0, st>>>(h->C, A);
+  adj_pull_kernel<<<g, 256, 0, st>>>(h->C, A);
   return cuda_err(cudaGetLastError());
+}
+
+// Recompute the states of a segment of len steps from its restored first state, then run
+// the reverse steps through them, starting from adjoint buffer cur.
+int tape_segment(lbmice_tape_t* t, int len, int cur, cudaStream_t st) {
+  int rc = LBMICE_OK;
+  for (int j = 0; j + 1 < len && rc == LBMICE_OK; ++j)
+    rc = launch_step_ptrs(t->h, tape_step_ptrs(t, j), st);
+  for (int j = len - 1; j >= 0 && rc == LBMICE_OK; --j) {
+    rc = tape_reverse_step(t, j, cur, st);
+    cur = 1 - cur;
+  }
+  return rc;
 }
 
 // [ny][nx] float array (host or device) <-> [ny][pitch] plane.
@@ -1157,12 +1174,23 @@ int lbmice_tape_backward(lbmice_tape_t* t, const float* phi_bar, const float* U_
     const int64_t s0 = c * t->every;
     const int len = (int)std::min<int64_t>(t->every, t->steps - s0);
     if ((rc = tape_restore(t, (size_t)c)) != LBMICE_OK) return rc;
-    for (int j = 0; j + 1 < len; ++j)
-      if ((rc = launch_step_ptrs(h, tape_step_ptrs(t, j), h->stream)) != LBMICE_OK) return rc;
-    for (int j = len - 1; j >= 0; --j) {
-      if ((rc = tape_reverse_step(t, j, cur)) != LBMICE_OK) return rc;
-      cur = 1 - cur;
+    if (len == t->every) {  // a full segment: replay its graph
+      if (!t->seg_graph[cur]) {
+        cudaGraph_t gr = nullptr;
+        LB_TRY(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
+        rc = tape_segment(t, len, cur, h->capture);
+        const cudaError_t e = cudaStreamEndCapture(h->capture, &gr);
+        if (rc != LBMICE_OK) { if (gr) cudaGraphDestroy(gr); return rc; }
+        if (e != cudaSuccess) return cuda_err(e);
+        const cudaError_t ei = cudaGraphInstantiate(&t->seg_graph[cur], gr, 0);
+        cudaGraphDestroy(gr);
+        if (ei != cudaSuccess) { t->seg_graph[cur] = nullptr; return cuda_err(ei); }
+      }
+      LB_TRY(cudaGraphLaunch(t->seg_graph[cur], h->stream));
+    } else if ((rc = tape_segment(t, len, cur, h->stream)) != LBMICE_OK) {
+      return rc;
     }
+    if (len & 1) cur = 1 - cur;
   }
   if (nseg == 0 && (rc = tape_restore(t, 0)) != LBMICE_OK) return rc;
   // initial state: adjoints of the moments it was built from
