@@ -106,6 +106,10 @@ typedef struct lbmice_params {
   int32_t flow;         /* 1: evolve the flow lattice f; 0: fluid at rest, f not stored    */
   int32_t check_every;  /* lbmice_step checks for NaN/Inf every this many steps (0: never) */
   int32_t storage;      /* LBMICE_STORAGE_* (default F32)                                  */
+  int32_t stencil;      /* gradient of phi (Sec. 3.1.1): 2 central difference, 4, 6 or 8 the
+                           isotropic stencils of Table 1 (default 4; 0 also means 4)       */
+  int32_t fold;         /* anisotropy symmetry: 6 (ice, Sec. 2.1, default; 0 also) or 4 (the
+                           four-fold validation system)                                    */
 } lbmice_params;
 
 typedef struct lbmice_ctx lbmice_t;

@@ -36,6 +36,7 @@ class OrcParams(ctypes.Structure):
         ("kappa_N", ctypes.c_double),
         ("U_in", ctypes.c_double), ("u_in", ctypes.c_double), ("nu", ctypes.c_double),
         ("bc", ctypes.c_int32 * 4), ("flow", ctypes.c_int32),
+        ("stencil", ctypes.c_int32), ("fold", ctypes.c_int32),
     ]
 
 
@@ -74,6 +75,9 @@ def lib():
         L.orc_gradient_periodic.argtypes = [dp, i32, i32, dp, dp]
         L.orc_anisotropy.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, dp]
+        L.orc_anisotropy_fold.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, i32, dp]
+        L.orc_gradient_stencil.argtypes = [dp, i32, i32, i32, dp, dp]
         L.orc_grad_run.argtypes = ([ctypes.POINTER(OrcParams)] + [dp] * 10 +
                                    [i64, dp, dp, i32, dp, dp])
         _lib = L
@@ -90,7 +94,7 @@ def _f64(a):
 
 def make_params(nx, ny, *, dx=0.4, dt=0.008, W0=1.0, tau0=1.0, D=2.0, lam=0.0, L_sat=1.0,
                 eps=0.05, kappa_N=1.0, U_in=0.0, u_in=0.0, nu=0.016,
-                bc=(BC_PERIODIC,) * 4, flow=False) -> OrcParams:
+                bc=(BC_PERIODIC,) * 4, flow=False, stencil=4, fold=6) -> OrcParams:
     p = OrcParams()
     p.nx, p.ny = int(nx), int(ny)
     p.dx, p.dt, p.W0, p.tau0 = dx, dt, W0, tau0
@@ -99,6 +103,7 @@ def make_params(nx, ny, *, dx=0.4, dt=0.008, W0=1.0, tau0=1.0, D=2.0, lam=0.0, L
     for i in range(4):
         p.bc[i] = int(bc[i])
     p.flow = 1 if flow else 0
+    p.stencil, p.fold = int(stencil), int(fold)
     return p
 
 
@@ -225,3 +230,21 @@ def grad_run(params: OrcParams, fields: dict, nsteps: int, wphi, wU, dfields: di
     if rc != 0:
         raise ValueError("oracle rejected the gradient run")
     return dict(zip(("L",) + GRAD_KEYS, out.tolist()))
+
+
+def gradient_stencil(phi, stencil: int = 4) -> tuple[np.ndarray, np.ndarray]:
+    """Gradient of a periodic field with the E2 / E4 / E6 / E8 stencil (Sec. 3.1.1)."""
+    f = np.ascontiguousarray(phi, dtype=np.float64)
+    ny, nx = f.shape
+    gx, gy = np.empty_like(f), np.empty_like(f)
+    if lib().orc_gradient_stencil(_dp(f), nx, ny, int(stencil), _dp(gx), _dp(gy)) != 0:
+        raise ValueError("bad stencil")
+    return gx, gy
+
+
+def anisotropy_fold(gx: float, gy: float, eps: float, kappa_N: float = 1.0, fold: int = 6):
+    """(a_s, N_x, N_y) for an anisotropy of the given symmetry fold (4 or 6)."""
+    out = np.zeros(3)
+    if lib().orc_anisotropy_fold(gx, gy, eps, kappa_N, int(fold), _dp(out)) != 0:
+        raise ValueError("bad fold")
+    return tuple(out.tolist())

@@ -98,6 +98,8 @@ typedef struct {
   double U_in, u_in, nu;
   int32_t bc[4];  // faces -x, +x, -y, +y
   int32_t flow;   // 1: flow lattice f is evolved; 0: fluid at rest, f absent
+  int32_t stencil;  // gradient of Sec. 3.1.1: 2 (central difference), 4, 6, 8 (Table 1); 0 = 4
+  int32_t fold;     // anisotropy symmetry: 6 (ice, Sec. 2.1) or 4 (validation case); 0 = 6
 } orc_params;
 
 }  // extern "C"
@@ -203,6 +205,45 @@ void grad_e4(T pE, T pW, T pN, T pS, T pNE, T pNW, T pSE, T pSW, T* gx, T* gy) {
   *gy = kWg1 * (pN - pS) + kWg2 * ((pNE - pSE) + (pNW - pSW));
 }
 
+// The gradient with the stencil of the run (Sec. 3.1.1): E2 is the central difference; E4, E6
+// and E8 sum w(|c|^2) phi(x + c) c over the neighbour shells of Table 1 (|c|^2 = 1, 2, 4, 5,
+// 8), with the weights as printed (they carry the 1/c_s^2, R2). P(dx, dy) is phi at the
+// offset. Every shell is a sum of differences of opposite neighbours, grouped so that a
+// mirrored field gives the exactly mirrored gradient.
+int stencil_of(const orc_params& p) { return p.stencil == 0 ? 4 : p.stencil; }
+int fold_of(const orc_params& p) { return p.fold == 0 ? 6 : p.fold; }
+
+template <class T, class F>
+void gradient_stencil(int stencil, F P, T* gx, T* gy) {
+  if (stencil == 2) {
+    *gx = 0.5 * (P(1, 0) - P(-1, 0));
+    *gy = 0.5 * (P(0, 1) - P(0, -1));
+    return;
+  }
+  double w1 = kWg1, w2 = kWg2, w4 = 0.0, w5 = 0.0, w8 = 0.0;
+  if (stencil == 6) {
+    w1 = 4.0 / 15.0; w2 = 1.0 / 10.0; w4 = 1.0 / 120.0;
+  } else if (stencil == 8) {
+    w1 = 4.0 / 21.0; w2 = 4.0 / 45.0; w4 = 1.0 / 60.0; w5 = 2.0 / 315.0; w8 = 1.0 / 5040.0;
+  }
+  T ax = w1 * (P(1, 0) - P(-1, 0)) + w2 * ((P(1, 1) - P(-1, 1)) + (P(1, -1) - P(-1, -1)));
+  T ay = w1 * (P(0, 1) - P(0, -1)) + w2 * ((P(1, 1) - P(1, -1)) + (P(-1, 1) - P(-1, -1)));
+  if (stencil >= 6) {
+    ax = ax + (2.0 * w4) * (P(2, 0) - P(-2, 0));
+    ay = ay + (2.0 * w4) * (P(0, 2) - P(0, -2));
+  }
+  if (stencil == 8) {
+    ax = ax + w5 * (((P(1, 2) - P(-1, 2)) + (P(1, -2) - P(-1, -2))) +
+                    2.0 * ((P(2, 1) - P(-2, 1)) + (P(2, -1) - P(-2, -1))));
+    ay = ay + w5 * (2.0 * ((P(1, 2) - P(1, -2)) + (P(-1, 2) - P(-1, -2))) +
+                    ((P(2, 1) - P(2, -1)) + (P(-2, 1) - P(-2, -1))));
+    ax = ax + (2.0 * w8) * ((P(2, 2) - P(-2, 2)) + (P(2, -2) - P(-2, -2)));
+    ay = ay + (2.0 * w8) * ((P(2, 2) - P(2, -2)) + (P(-2, 2) - P(-2, -2)));
+  }
+  *gx = ax;
+  *gy = ay;
+}
+
 // ---------------------------------------------------------------------------------------
 // Six-fold anisotropy (Sec. 2.1): a_s(n) = 1 + eps cos(6 theta), theta the angle of the
 // interface normal n = -grad phi / |grad phi| (R3, R4), and the anisotropic flux of Eq. (a)
@@ -211,7 +252,7 @@ void grad_e4(T pE, T pW, T pN, T pS, T pNE, T pNW, T pSE, T pSW, T* gx, T* gy) {
 // so N = kappa_N a_s 6 eps sin(6 theta) (g_y, -g_x). N is linear in g and carries its units.
 // ---------------------------------------------------------------------------------------
 template <class T, class P>
-void anisotropy(T gx, T gy, P eps, double kappa_N, T* as, T* Nx, T* Ny) {
+void anisotropy(T gx, T gy, P eps, double kappa_N, int fold, T* as, T* Nx, T* Ny) {
   const T s = gx * gx + gy * gy;
   if (!(s > kGradEps)) {
     *as = T(1.0);
@@ -225,6 +266,17 @@ void anisotropy(T gx, T gy, P eps, double kappa_N, T* as, T* Nx, T* Ny) {
   const T ny = gy / r;
   const T X = nx * nx;
   const T Y = ny * ny;
+  if (fold == 4) {
+    // the four-fold validation case: cos(4 theta), sin(4 theta) from (n_x + i n_y)^4, and
+    // |g|^2 da_s/dg = 4 eps sin(4 theta) (g_y, -g_x)
+    const T cos4 = X * X - 6.0 * X * Y + Y * Y;
+    const T sin4 = 4.0 * nx * ny * (X - Y);
+    *as = 1.0 + eps * cos4;
+    const T t4 = kappa_N * (*as) * (4.0 * eps) * sin4;
+    *Nx = t4 * gy;
+    *Ny = -(t4 * gx);
+    return;
+  }
   // cos(6 theta) and sin(6 theta) as the real and imaginary parts of (n_x + i n_y)^6.
   const T cos6 = X * X * X - 15.0 * X * X * Y + 15.0 * X * Y * Y - Y * Y * Y;
   const T sin6 = nx * ny * (6.0 * X * X - 20.0 * X * Y + 6.0 * Y * Y);
@@ -265,6 +317,9 @@ bool derive(const orc_params& p, Derived* d) {
     if (p.bc[f] < BC_PERIODIC || p.bc[f] > BC_FREESLIP) return false;
   if ((p.bc[0] == BC_PERIODIC) != (p.bc[1] == BC_PERIODIC)) return false;
   if ((p.bc[2] == BC_PERIODIC) != (p.bc[3] == BC_PERIODIC)) return false;
+  if (p.stencil != 0 && p.stencil != 2 && p.stencil != 4 && p.stencil != 6 && p.stencil != 8)
+    return false;
+  if (p.fold != 0 && p.fold != 4 && p.fold != 6) return false;
   d->Dphi = (p.W0 * p.W0 / p.tau0) * p.dt / (p.dx * p.dx);
   d->dt_tau0 = p.dt / p.tau0;
   d->Dlat = p.D * p.dt / (p.dx * p.dx);
@@ -314,10 +369,8 @@ T phi_ghost(const Oracle<T>& o, const std::vector<T>& phi, int x, int y) {
 
 template <class T>
 void gradient_at(const Oracle<T>& o, const std::vector<T>& phi, int x, int y, T* gx, T* gy) {
-  grad_e4(phi_ghost(o, phi, x + 1, y), phi_ghost(o, phi, x - 1, y),
-          phi_ghost(o, phi, x, y + 1), phi_ghost(o, phi, x, y - 1),
-          phi_ghost(o, phi, x + 1, y + 1), phi_ghost(o, phi, x - 1, y + 1),
-          phi_ghost(o, phi, x + 1, y - 1), phi_ghost(o, phi, x - 1, y - 1), gx, gy);
+  auto P = [&](int dx, int dy) { return phi_ghost(o, phi, x + dx, y + dy); };
+  gradient_stencil(stencil_of(o.p), P, gx, gy);
 }
 
 // Fluid velocity of a node (R10): u = j / (rho + k/2) and the solid-damped u* = (1-phi)/2 u.
@@ -369,7 +422,7 @@ void collide(Oracle<T>* o) {
       // Gradient, anisotropy and the phase-field relaxation time (Sec. 2.2.3).
       T gx, gy, as, Nx, Ny;
       gradient_at(*o, phi, x, y, &gx, &gy);
-      anisotropy(gx, gy, o->eps, p.kappa_N, &as, &Nx, &Ny);
+      anisotropy(gx, gy, o->eps, p.kappa_N, fold_of(p), &as, &Nx, &Ny);
       const T a2 = as * as;
       const T eta = 3.0 * a2 * d.Dphi + 0.5;
       const T Qphi = ph - ph * ph * ph + o->lambda * U * (1.0 - ph * ph) * (1.0 - ph * ph);
@@ -495,7 +548,7 @@ void init_fields_t(Oracle<T>* o, const std::vector<T>& phi, const std::vector<T>
       const size_t i = o->at(x, y);
       T gx, gy, as, Nx, Ny;
       gradient_at(*o, phi, x, y, &gx, &gy);
-      anisotropy(gx, gy, o->eps, o->p.kappa_N, &as, &Nx, &Ny);
+      anisotropy(gx, gy, o->eps, o->p.kappa_N, fold_of(o->p), &as, &Nx, &Ny);
       // without the flow lattice the fluid is at rest (rho = 1, u = 0)
       const bool fl = o->p.flow != 0;
       const T rho = (fl && !rho0.empty()) ? rho0[i] : T(1.0);
@@ -740,7 +793,31 @@ int orc_gradient_periodic(const double* phi, int nx, int ny, double* gx, double*
 // a_s and N (Sec. 2.1, R1) for one gradient vector: out = {a_s, N_x, N_y}.
 int orc_anisotropy(double gx, double gy, double eps, double kappa_N, double out[3]) {
   if (!out) return -1;
-  anisotropy(gx, gy, eps, kappa_N, &out[0], &out[1], &out[2]);
+  anisotropy(gx, gy, eps, kappa_N, 6, &out[0], &out[1], &out[2]);
+  return 0;
+}
+
+// a_s and N for a given symmetry fold (4 or 6).
+int orc_anisotropy_fold(double gx, double gy, double eps, double kappa_N, int fold,
+                        double out[3]) {
+  if (!out || (fold != 4 && fold != 6)) return -1;
+  anisotropy(gx, gy, eps, kappa_N, fold, &out[0], &out[1], &out[2]);
+  return 0;
+}
+
+// Gradient of a periodic field with a given stencil (2, 4, 6, 8), lattice units.
+int orc_gradient_stencil(const double* phi, int nx, int ny, int stencil, double* gx,
+                         double* gy) {
+  if (!phi || !gx || !gy || nx < 1 || ny < 1) return -1;
+  if (stencil != 2 && stencil != 4 && stencil != 6 && stencil != 8) return -1;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      auto P = [&](int dx, int dy) {
+        const int xx = (((x + dx) % nx) + nx) % nx, yy = (((y + dy) % ny) + ny) % ny;
+        return phi[(size_t)yy * nx + xx];
+      };
+      gradient_stencil(stencil, P, &gx[(size_t)y * nx + x], &gy[(size_t)y * nx + x]);
+    }
   return 0;
 }
 

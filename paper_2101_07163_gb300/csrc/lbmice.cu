@@ -9,6 +9,7 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -88,6 +89,9 @@ int validate(const lbmice_params& p) {
   if (p.flow != 0 && p.flow != 1) return LBMICE_EINVAL;
   if (p.check_every < 0) return LBMICE_EINVAL;
   if (p.storage < LBMICE_STORAGE_F32 || p.storage > LBMICE_STORAGE_BF16) return LBMICE_EINVAL;
+  if (p.stencil != 0 && p.stencil != 2 && p.stencil != 4 && p.stencil != 6 && p.stencil != 8)
+    return LBMICE_EINVAL;
+  if (p.fold != 0 && p.fold != 4 && p.fold != 6) return LBMICE_EINVAL;
   if (!std::isfinite(p.u_in) || std::fabs(p.u_in) >= std::sqrt(1.0 / 3.0)) return LBMICE_EUNSTABLE;
   if (p.flow && !(p.nu > 0)) return LBMICE_EUNSTABLE;  // tau_f = 3 nu + 1/2 must exceed 1/2
   return LBMICE_OK;
@@ -103,6 +107,8 @@ void derive(lbmice_t* h) {
   C.pstride = (long long)C.pitch * p.ny;  // plane-major: [plane][ny][pitch]
   C.rstride = C.pitch;
   for (int f = 0; f < 4; ++f) C.bc[f] = p.bc[f];
+  C.stencil = p.stencil == 0 ? 4 : p.stencil;
+  C.fold = p.fold == 0 ? 6 : p.fold;
   const double Dphi = (p.W0 * p.W0 / p.tau0) * p.dt / (p.dx * p.dx);
   h->Dphi3 = 3.0 * Dphi;
   h->lambda = p.lambda > 0 ? p.lambda : p.tau0 * p.D / (kA2 * p.W0 * p.W0);
@@ -114,7 +120,7 @@ void derive(lbmice_t* h) {
   C.Dlat3 = (float)(3.0 * p.D * p.dt / (p.dx * p.dx));
   C.half_Lsat = (float)(0.5 * p.L_sat);
   C.eps = (float)p.eps;
-  C.kN6eps = (float)(p.kappa_N * 6.0 * p.eps);
+  C.kNkeps = (float)(p.kappa_N * C.fold * p.eps);
   C.kdrag = (float)(kHdrag * p.nu / (4.0 * Wlat * Wlat));
   C.inv_tau_f = (float)(1.0 / tau_f);
   C.guo = (float)(1.0 - 0.5 / tau_f);
@@ -163,16 +169,22 @@ int with_storage(const lbmice_t* h, Fn&& fn) {
 // One step of grid h on the given buffers.
 int launch_step_ptrs(const lbmice_t* h, const StepPtrs& P, cudaStream_t st) {
   const dim3 grd((h->C.nx + kTX - 1) / kTX, (h->C.ny + kTY - 1) / kTY), blk(kTX * kTY);
-  return with_storage(h, [&](auto tag) {
-    using S = decltype(tag);
-    if (h->p.flow)
-      step_kernel<kTX, kTY, true, S>
-          <<<grd, blk, Tile<kTX, kTY>::smem_bytes<true>(), st>>>(h->C, P);
-    else
-      step_kernel<kTX, kTY, false, S>
-          <<<grd, blk, Tile<kTX, kTY>::smem_bytes<false>(), st>>>(h->C, P);
-    return cuda_err(cudaGetLastError());
-  });
+  auto launch = [&](auto radius) {
+    constexpr int R = decltype(radius)::value;
+    return with_storage(h, [&](auto tag) {
+      using S = decltype(tag);
+      if (h->p.flow)
+        step_kernel<kTX, kTY, true, S, R>
+            <<<grd, blk, Tile<kTX, kTY, R>::template smem_bytes<true>(), st>>>(h->C, P);
+      else
+        step_kernel<kTX, kTY, false, S, R>
+            <<<grd, blk, Tile<kTX, kTY, R>::template smem_bytes<false>(), st>>>(h->C, P);
+      return cuda_err(cudaGetLastError());
+    });
+  };
+  // E6 and E8 reach two nodes out: their kernels hold a phi halo of 3
+  return h->C.stencil >= 6 ? launch(std::integral_constant<int, 2>{})
+                           : launch(std::integral_constant<int, 1>{});
 }
 
 // Step s of grid h on its own rotating buffers.
@@ -228,16 +240,16 @@ int equilibrium_from(lbmice_t* h, const double* phi, const double* U, const doub
   if (!h->p.flow) ux = uy = rho = nullptr;  // fluid at rest: g^eq sees u = 0
   const dim3 blk(32, 8);
   const dim3 grd = node_grid(h->C, blk);
-  const double eps = h->p.eps, kN6eps = h->p.kappa_N * 6.0 * h->p.eps;
+  const double eps = h->p.eps, kNkeps = h->p.kappa_N * h->C.fold * h->p.eps;
   int rc = with_storage(h, [&](auto tag) {
     using S = decltype(tag);
     if (h->p.flow)
       equilibrium_kernel<true, S><<<grd, blk, 0, h->stream>>>(
-          h->C, h->Dphi3, eps, kN6eps, phi, U, rho, ux, uy, h->pops[0], h->phi[0], h->phi[2],
+          h->C, h->Dphi3, eps, kNkeps, phi, U, rho, ux, uy, h->pops[0], h->phi[0], h->phi[2],
           h->Um[0], h->rhom[0]);
     else
       equilibrium_kernel<false, S><<<grd, blk, 0, h->stream>>>(
-          h->C, h->Dphi3, eps, kN6eps, phi, U, rho, ux, uy, h->pops[0], h->phi[0], h->phi[2],
+          h->C, h->Dphi3, eps, kNkeps, phi, U, rho, ux, uy, h->pops[0], h->phi[0], h->phi[2],
           h->Um[0], h->rhom[0]);
     return cuda_err(cudaGetLastError());
   });
@@ -266,6 +278,8 @@ int lbmice_params_default(lbmice_params* p, int32_t nx, int32_t ny) {
   p->kappa_N = 1.0;
   p->nu = 0.016;
   for (int f = 0; f < 4; ++f) p->bc[f] = LBMICE_BC_PERIODIC;
+  p->stencil = 4;
+  p->fold = 6;
   return LBMICE_OK;
 }
 
@@ -787,6 +801,7 @@ int lbmice_batch_create(const lbmice_params* params, int32_t count, void* stream
   for (int i = 0; i < count; ++i) {
     if (params[i].flow != params[0].flow || params[i].storage != params[0].storage)
       return LBMICE_EINVAL;
+    if (params[i].stencil == 6 || params[i].stencil == 8) return LBMICE_EINVAL;
     const int rc = validate(params[i]);
     if (rc != LBMICE_OK) return rc;
   }
@@ -1112,6 +1127,7 @@ int lbmice_tape_create(lbmice_t* h, int32_t every, lbmice_tape_t** out) {
   if (!out) return LBMICE_EINVAL;
   *out = nullptr;
   if (!h || every < 1 || !tape_supported(h) || h->step != 0) return LBMICE_EINVAL;
+  if (h->C.stencil != 4 || h->C.fold != 6) return LBMICE_EINVAL;  // the adjoint's E4, six-fold
   lbmice_tape_t* t = new (std::nothrow) lbmice_tape();
   if (!t) return LBMICE_ENOMEM;
   t->h = h;

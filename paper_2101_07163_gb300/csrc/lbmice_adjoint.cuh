@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(const Consts C, const 
       cos6 = X2 * X2 * X2 - 15.0f * X2 * X2 * Y2 + 15.0f * X2 * Y2 * Y2 - Y2 * Y2 * Y2;
       sin6 = nx * ny * (6.0f * X2 * X2 - 20.0f * X2 * Y2 + 6.0f * Y2 * Y2);
       as = 1.0f + C.eps * cos6;
-      t = C.kN6eps * as * sin6;
+      t = C.kNkeps * as * sin6;
       Nx = t * gy;
       Ny = -(t * gx);
     }
@@ -192,14 +192,14 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(const Consts C, const 
     phb += srcQ_b * C.dt_tau0 * (1.0f - 3.0f * ph * ph - 4.0f * C.lambda * U * omp2 * ph);
     Ub += srcQ_b * C.dt_tau0 * C.lambda * omp2 * omp2;
     part[ADJ_LAMBDA] += (double)(srcQ_b * C.dt_tau0 * U * omp2 * omp2);
-    // anisotropy: N = t (g_y, -g_x), t = kN6eps a_s sin6, a_s = 1 + eps cos6, n = g / |g|
+    // anisotropy: N = t (g_y, -g_x), t = kNkeps a_s sin6, a_s = 1 + eps cos6, n = g / |g|
     float gxb = 0.0f, gyb = 0.0f;
     if (aniso_on) {
       const float tb = Nxb * gy - Nyb * gx;
       gyb += Nxb * t;
       gxb -= Nyb * t;
-      as_b += tb * C.kN6eps * sin6;
-      const float sin6_b = tb * C.kN6eps * as;
+      as_b += tb * C.kNkeps * sin6;
+      const float sin6_b = tb * C.kNkeps * as;
       part[ADJ_KN6EPS] += (double)(tb * as * sin6);
       const float cos6_b = as_b * C.eps;
       part[ADJ_EPS] += (double)(as_b * cos6);
@@ -421,12 +421,12 @@ __global__ void __launch_bounds__(256) adj_init_kernel(const Consts C, const Ini
       const float Pp = 6.0f * X2 * X2 - 20.0f * X2 * Y2 + 6.0f * Y2 * Y2;
       const float sin6 = nx * ny * Pp;
       const float as = 1.0f + C.eps * cos6;
-      const float t = C.kN6eps * as * sin6;
+      const float t = C.kNkeps * as * sin6;
       const float tb = Nxb * gy - Nyb * gx;
       gyb += Nxb * t;
       gxb -= Nyb * t;
-      const float as_b = tb * C.kN6eps * sin6;
-      const float sin6_b = tb * C.kN6eps * as;
+      const float as_b = tb * C.kNkeps * sin6;
+      const float sin6_b = tb * C.kNkeps * as;
       part[ADJ_KN6EPS] += (double)(tb * as * sin6);
       const float cos6_b = as_b * C.eps;
       part[ADJ_EPS] += (double)(as_b * cos6);

@@ -29,11 +29,12 @@ __global__ void seed_kernel(int nx, int ny, double cx, double cy, double R0, dou
 }
 
 // Populations at the equilibria of given moments, computed in double and stored in the
-// storage type: h^eq (Eq. (e)) with the anisotropic flux of the E4 gradient of phi, g^eq
-// (Sec. 2.2.2), f^eq (Sec. 2.2.1). The stored phi and its history both become sum h; with
+// storage type: h^eq (Eq. (e)) with the anisotropic flux of the gradient of phi, g^eq
+// (Sec. 2.2.2), f^eq (Sec. 2.2.1), the gradient with the run's stencil and the anisotropy
+// with its fold. The stored phi and its history both become sum h; with
 // 16-bit storage U and rho become sum g and sum f.
 template <bool FLOW, class S>
-__global__ void equilibrium_kernel(const Consts C, double Dphi3, double eps, double kN6eps,
+__global__ void equilibrium_kernel(const Consts C, double Dphi3, double eps, double kNkeps,
                                    const double* __restrict__ phi0,
                                    const double* __restrict__ U0,
                                    const double* __restrict__ rho0,
@@ -53,14 +54,11 @@ __global__ void equilibrium_kernel(const Consts C, double Dphi3, double eps, dou
   };
   const long long i = (long long)Y * C.nx + X;
   const double ph = phi0[i];
-  const double gx = (1.0 / 3.0) * (P(X + 1, Y) - P(X - 1, Y)) +
-                    (1.0 / 12.0) * ((P(X + 1, Y + 1) - P(X - 1, Y + 1)) +
-                                    (P(X + 1, Y - 1) - P(X - 1, Y - 1)));
-  const double gy = (1.0 / 3.0) * (P(X, Y + 1) - P(X, Y - 1)) +
-                    (1.0 / 12.0) * ((P(X + 1, Y + 1) - P(X + 1, Y - 1)) +
-                                    (P(X - 1, Y + 1) - P(X - 1, Y - 1)));
+  double gx, gy;
+  gradient_stencil<double>(C.stencil, [&](int dx, int dy) { return P(X + dx, Y + dy); }, gx,
+                           gy);
   double as, Nx, Ny;
-  aniso(gx, gy, eps, kN6eps, as, Nx, Ny);
+  aniso(gx, gy, eps, kNkeps, C.fold, as, Nx, Ny);
   const double U = U0[i];
   const double rho = rho0 ? rho0[i] : 1.0;
   const double ux = ux0 ? ux0[i] : 0.0;

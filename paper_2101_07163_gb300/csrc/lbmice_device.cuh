@@ -221,6 +221,8 @@ enum : int { PLANE_H = 0, PLANE_G = 9, PLANE_F = 18 };
 struct Consts {
   int nx, ny, pitch;  // pitch: floats per row of a phi array
   int bc[4];
+  int stencil;        // gradient stencil (Sec. 3.1.1): 2, 4, 6 or 8
+  int fold;           // anisotropy symmetry: 6 (ice, Sec. 2.1) or 4 (validation case)
   long long pstride;  // floats between population planes of one node
   long long rstride;  // floats between rows of one population plane
   float Dphi3;       // 3 (W0^2/tau0) dt/dx^2: eta = Dphi3 a_s^2 + 1/2, h^eq flux weight
@@ -229,7 +231,7 @@ struct Consts {
   float Dlat3;       // 3 D dt/dx^2: tau_g = Dlat3 q + 1/2
   float half_Lsat;   // L_sat / 2
   float eps;         // six-fold anisotropy strength
-  float kN6eps;      // kappa_N * 6 eps: N = kN6eps a_s sin(6 theta) (g_y, -g_x)
+  float kNkeps;      // kappa_N k eps (k = fold): N = kNkeps a_s sin(k theta) (g_y, -g_x)
   float kdrag;       // h nu / (4 (W0/dx)^2): k = kdrag rho (1+phi)^2 (1-phi)
   float inv_tau_f;   // 1 / tau_f
   float guo;         // 1 - 1/(2 tau_f)
@@ -245,7 +247,8 @@ __device__ constexpr float kW2 = 1.0f / 12.0f;
 // anisotropic flux N = kappa_N a_s 6 eps sin(6 theta) (g_y, -g_x). cos/sin(6 theta) are the
 // real/imaginary parts of (n_x + i n_y)^6 of the unit normal; |g|^2 <= 1e-12 -> isotropic.
 template <class T>
-__device__ __forceinline__ void aniso(T gx, T gy, T eps, T kN6eps, T& as, T& Nx, T& Ny) {
+__device__ __forceinline__ void aniso(T gx, T gy, T eps, T kNkeps, int fold, T& as, T& Nx,
+                                      T& Ny) {
   const T s = gx * gx + gy * gy;
   as = T(1);
   Nx = T(0);
@@ -254,18 +257,64 @@ __device__ __forceinline__ void aniso(T gx, T gy, T eps, T kN6eps, T& as, T& Nx,
     const T rinv = T(1) / sqrt(s);
     const T nx = gx * rinv, ny = gy * rinv;
     const T X = nx * nx, Y = ny * ny;
-    const T cos6 = X * X * X - T(15) * X * X * Y + T(15) * X * Y * Y - Y * Y * Y;
-    const T sin6 = nx * ny * (T(6) * X * X - T(20) * X * Y + T(6) * Y * Y);
-    as = T(1) + eps * cos6;
-    const T t = kN6eps * as * sin6;
+    T cosk, sink;
+    if (fold == 4) {  // cos/sin(4 theta) from (n_x + i n_y)^4
+      cosk = X * X - T(6) * X * Y + Y * Y;
+      sink = T(4) * nx * ny * (X - Y);
+    } else {
+      cosk = X * X * X - T(15) * X * X * Y + T(15) * X * Y * Y - Y * Y * Y;
+      sink = nx * ny * (T(6) * X * X - T(20) * X * Y + T(6) * Y * Y);
+    }
+    as = T(1) + eps * cosk;
+    const T t = kNkeps * as * sink;
     Nx = t * gy;
     Ny = -(t * gx);
   }
 }
 
+// Isotropic gradient with the stencil of the run (Sec. 3.1.1): E2 is the central difference;
+// E4, E6, E8 sum w(|c|^2) phi(x + c) c over the neighbour shells of Table 1 with the printed
+// weights (they carry the 1/c_s^2). P(dx, dy) is phi at the offset. Every shell is a sum of
+// differences of opposite neighbours, grouped so that mirrored fields give exactly mirrored
+// gradients; E4 is written exactly as the kernels always computed it.
+template <class T, class F>
+__device__ __forceinline__ void gradient_stencil(int stencil, F P, T& gx, T& gy) {
+  if (stencil == 2) {
+    gx = T(0.5) * (P(1, 0) - P(-1, 0));
+    gy = T(0.5) * (P(0, 1) - P(0, -1));
+    return;
+  }
+  if (stencil == 4) {
+    gx = T(1.0 / 3.0) * (P(1, 0) - P(-1, 0)) +
+         T(1.0 / 12.0) * ((P(1, 1) - P(-1, 1)) + (P(1, -1) - P(-1, -1)));
+    gy = T(1.0 / 3.0) * (P(0, 1) - P(0, -1)) +
+         T(1.0 / 12.0) * ((P(1, 1) - P(1, -1)) + (P(-1, 1) - P(-1, -1)));
+    return;
+  }
+  const bool e8 = stencil == 8;
+  const T w1 = e8 ? T(4.0 / 21.0) : T(4.0 / 15.0);
+  const T w2 = e8 ? T(4.0 / 45.0) : T(1.0 / 10.0);
+  const T w4x2 = e8 ? T(2.0 / 60.0) : T(2.0 / 120.0);
+  T ax = w1 * (P(1, 0) - P(-1, 0)) + w2 * ((P(1, 1) - P(-1, 1)) + (P(1, -1) - P(-1, -1)));
+  T ay = w1 * (P(0, 1) - P(0, -1)) + w2 * ((P(1, 1) - P(1, -1)) + (P(-1, 1) - P(-1, -1)));
+  ax = ax + w4x2 * (P(2, 0) - P(-2, 0));
+  ay = ay + w4x2 * (P(0, 2) - P(0, -2));
+  if (e8) {
+    const T w5 = T(2.0 / 315.0), w8x2 = T(2.0 / 5040.0);
+    ax = ax + w5 * (((P(1, 2) - P(-1, 2)) + (P(1, -2) - P(-1, -2))) +
+                    T(2) * ((P(2, 1) - P(-2, 1)) + (P(2, -1) - P(-2, -1))));
+    ay = ay + w5 * (T(2) * ((P(1, 2) - P(1, -2)) + (P(-1, 2) - P(-1, -2))) +
+                    ((P(2, 1) - P(2, -1)) + (P(-2, 1) - P(-2, -1))));
+    ax = ax + w8x2 * ((P(2, 2) - P(-2, 2)) + (P(2, -2) - P(-2, -2)));
+    ay = ay + w8x2 * ((P(2, 2) - P(2, -2)) + (P(-2, 2) - P(-2, -2)));
+  }
+  gx = ax;
+  gy = ay;
+}
+
 // Ghost resolution of one axis for phi reads (R: periodic wrap, zero-gradient clamp,
 // free-slip reflection about the wall half a cell out, inlet = vapour). Returns false for
-// an inlet ghost. Valid for coordinates up to two cells outside.
+// an inlet ghost. Valid for coordinates up to a grid length outside.
 __device__ __forceinline__ bool axis_phi(int v, int n, int bc_lo, int bc_hi, int& out) {
   if (v < 0) {
     if (bc_lo == BC_PERIODIC) { out = v + n; return true; }

@@ -34,10 +34,14 @@ struct StepPtrs {
   float* __restrict__ rho_np1;
 };
 
-template <int TX, int TY>
+// Tile of TX x TY destination nodes for a gradient stencil of radius R (1: E2/E4, 2: E6/E8):
+// the phi tile has a halo of R + 1 (the stencil around every ring node), the collided source
+// tile a halo of 1.
+template <int TX, int TY, int R = 1>
 struct Tile {
-  static constexpr int PW = TX + 4;                  // phi tile row (halo 2)
-  static constexpr int PN = PW * (TY + 4);
+  static constexpr int H = R + 1;
+  static constexpr int PW = TX + 2 * H;              // phi tile row
+  static constexpr int PN = PW * (TY + 2 * H);
   static constexpr int SW = TX + 2;                  // source tile row (halo 1)
   static constexpr int SN = SW * (TY + 2);
   static constexpr int NRING = SN - TX * TY;
@@ -104,12 +108,12 @@ struct FactoredCollision {
 // coordinates (X, Y) in [-1, nx] x [-1, ny], and store its post-collision populations.
 // Ghost positions take the collision of the node their face rule maps them to (directions
 // mirrored across a free-slip wall), or the fixed inlet state.
-template <int TX, int TY, bool FLOW, class S, bool OWN>
+template <int TX, int TY, bool FLOW, class S, bool OWN, int R>
 __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& P, int X, int Y,
                                                int sx, int sy, const float* __restrict__ sphi,
                                                float* __restrict__ spost,
                                                float* __restrict__ sB, float* hown) {
-  using T = Tile<TX, TY>;
+  using T = Tile<TX, TY, R>;
   const int node = sy * T::SW + sx;
   int mx = X, my = Y, lx = sx, ly = sy;
   bool mirx = false, miry = false;
@@ -174,7 +178,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   }
 
   // ---- populations and moments at time n (Sec. 2.2) ----
-  const int pc = (ly + 1) * T::PW + (lx + 1);
+  const int pc = (ly + R) * T::PW + (lx + R);
   const float ph = sphi[pc];
   float hv[9], gv[9], fv[9];
   if constexpr (!ST::DEV) {
@@ -195,13 +199,19 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     jy = sumcy9(fv);
   }
 
-  // ---- E4 gradient of phi (Sec. 3.1.1, Table 1) and anisotropy (Sec. 2.1) ----
-  const float pE = sphi[pc + 1], pW = sphi[pc - 1];
-  const float pN = sphi[pc + T::PW], pS = sphi[pc - T::PW];
-  const float pNE = sphi[pc + T::PW + 1], pNW = sphi[pc + T::PW - 1];
-  const float pSE = sphi[pc - T::PW + 1], pSW = sphi[pc - T::PW - 1];
-  const float gx = kW1 * (pE - pW) + kW2 * ((pNE - pNW) + (pSE - pSW));
-  const float gy = kW1 * (pN - pS) + kW2 * ((pNE - pSE) + (pNW - pSW));
+  // ---- gradient of phi (Sec. 3.1.1, Table 1) and anisotropy (Sec. 2.1) ----
+  float gx, gy;
+  if (R == 1 && C.stencil != 2) {  // E4 (the default)
+    const float pE = sphi[pc + 1], pW = sphi[pc - 1];
+    const float pN = sphi[pc + T::PW], pS = sphi[pc - T::PW];
+    const float pNE = sphi[pc + T::PW + 1], pNW = sphi[pc + T::PW - 1];
+    const float pSE = sphi[pc - T::PW + 1], pSW = sphi[pc - T::PW - 1];
+    gx = kW1 * (pE - pW) + kW2 * ((pNE - pNW) + (pSE - pSW));
+    gy = kW1 * (pN - pS) + kW2 * ((pNE - pSE) + (pNW - pSW));
+  } else {  // E2, or E6 / E8 on a tile of halo R + 1 = 3
+    gradient_stencil<float>(C.stencil, [&](int dx, int dy) { return sphi[pc + dy * T::PW + dx]; },
+                            gx, gy);
+  }
   float as = 1.0f, Nx = 0.0f, Ny = 0.0f;
   {
     const float s2 = gx * gx + gy * gy;
@@ -209,11 +219,16 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
       const float rinv = rsqrtf(s2);
       const float nx = gx * rinv, ny = gy * rinv;
       const float X2 = nx * nx, Y2 = ny * ny;
-      const float cos6 =
-          X2 * X2 * X2 - 15.0f * X2 * X2 * Y2 + 15.0f * X2 * Y2 * Y2 - Y2 * Y2 * Y2;
-      const float sin6 = nx * ny * (6.0f * X2 * X2 - 20.0f * X2 * Y2 + 6.0f * Y2 * Y2);
-      as = 1.0f + C.eps * cos6;
-      const float t = C.kN6eps * as * sin6;
+      float cosk, sink;
+      if (C.fold == 4) {  // the four-fold validation case: cos/sin(4 theta)
+        cosk = X2 * X2 - 6.0f * X2 * Y2 + Y2 * Y2;
+        sink = 4.0f * nx * ny * (X2 - Y2);
+      } else {  // six-fold (ice): cos/sin(6 theta)
+        cosk = X2 * X2 * X2 - 15.0f * X2 * X2 * Y2 + 15.0f * X2 * Y2 * Y2 - Y2 * Y2 * Y2;
+        sink = nx * ny * (6.0f * X2 * X2 - 20.0f * X2 * Y2 + 6.0f * Y2 * Y2);
+      }
+      as = 1.0f + C.eps * cosk;
+      const float t = C.kNkeps * as * sink;
       Nx = t * gy;
       Ny = -(t * gx);
     }
@@ -291,22 +306,23 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
 }
 
 // One TX x TY tile with origin (x0, y0), computed by the TX * TY threads of the CTA (thread
-// tid owns node (x0 + tid % TX, y0 + tid / TX)). smem holds Tile<TX, TY>::smem_bytes.
-template <int TX, int TY, bool FLOW, class S>
+// tid owns node (x0 + tid % TX, y0 + tid / TX)). smem holds Tile<TX, TY, R>::smem_bytes.
+template <int TX, int TY, bool FLOW, class S, int R = 1>
 __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, int x0, int y0,
                                           float* smem) {
   using ST = Storage<S>;
-  using T = Tile<TX, TY>;
+  using T = Tile<TX, TY, R>;
+  constexpr int H = T::H;
   float* sphi = smem;
   float* spost = sphi + T::PN;
   float* sB = spost + (FLOW ? 27 : 18) * T::SN;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
 
-  // ---- A: phi^n with a two-node halo ----
-  if (x0 >= 2 && y0 >= 2 && x0 + TX + 2 <= C.nx && y0 + TY + 2 <= C.ny) {
+  // ---- A: phi^n with a halo of H = R + 1 nodes ----
+  if (x0 >= H && y0 >= H && x0 + TX + H <= C.nx && y0 + TY + H <= C.ny) {
     // the halo lies inside the grid (almost every tile): no ghost resolution
-    const float* __restrict__ pb = P.phi_n + (long long)(y0 - 2) * C.pitch + (x0 - 2);
+    const float* __restrict__ pb = P.phi_n + (long long)(y0 - H) * C.pitch + (x0 - H);
     const int pitch = (int)C.pitch;
     for (int i = tid; i < T::PN; i += T::NT) {
       const int lx = i % T::PW, ly = i / T::PW;
@@ -315,11 +331,11 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
   } else
   for (int i = tid; i < T::PN; i += T::NT) {
     const int lx = i % T::PW, ly = i / T::PW;
-    const int X = x0 - 2 + lx, Y = y0 - 2 + ly;
+    const int X = x0 - H + lx, Y = y0 - H + ly;
     int gx, gy;
     float v = -1.0f;
-    if (X > C.nx + 1 || Y > C.ny + 1) {
-      v = 0.0f;  // beyond the grid's two-node halo (ragged last tile): never read
+    if (X > C.nx + R || Y > C.ny + R) {
+      v = 0.0f;  // beyond the grid's halo (ragged last tile): never read
     } else if (axis_phi(X, C.nx, C.bc[0], C.bc[1], gx) &&
                axis_phi(Y, C.ny, C.bc[2], C.bc[3], gy)) {
       v = __ldg(P.phi_n + (long long)gy * C.pitch + gx);
@@ -333,7 +349,8 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
   {
     const int X = x0 + tx, Y = y0 + ty;
     if (X <= C.nx && Y <= C.ny)
-      collide_source<TX, TY, FLOW, S, true>(C, P, X, Y, tx + 1, ty + 1, sphi, spost, sB, hown);
+      collide_source<TX, TY, FLOW, S, true, R>(C, P, X, Y, tx + 1, ty + 1, sphi, spost, sB,
+                                               hown);
   }
   for (int r = tid; r < T::NRING; r += T::NT) {
     // ring order: bottom row, top row, then left and right columns
@@ -343,7 +360,7 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
     else { const int k = r - 2 * T::SW; sy = 1 + (k >> 1); sx = (k & 1) ? TX + 1 : 0; }
     const int X = x0 - 1 + sx, Y = y0 - 1 + sy;
     if (X >= -1 && X <= C.nx && Y >= -1 && Y <= C.ny)
-      collide_source<TX, TY, FLOW, S, false>(C, P, X, Y, sx, sy, sphi, spost, sB, nullptr);
+      collide_source<TX, TY, FLOW, S, false, R>(C, P, X, Y, sx, sy, sphi, spost, sB, nullptr);
   }
   __syncthreads();
 
@@ -398,17 +415,17 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
 // One CTA per TX x TY tile. FP32 storage is held to 64 registers (4 CTAs of 256 threads per
 // SM, the measured optimum); the 16-bit forms keep the compiler's own allocation, which a
 // minimum-blocks bound would change.
-template <int TX, int TY, bool FLOW, class S>
+template <int TX, int TY, bool FLOW, class S, int R>
 __global__ std::enable_if_t<!Storage<S>::DEV> __launch_bounds__(TX* TY, 4)
     step_kernel(const Consts C, const StepPtrs P) {
   extern __shared__ float smem[];
-  step_tile<TX, TY, FLOW, S>(C, P, blockIdx.x * TX, blockIdx.y * TY, smem);
+  step_tile<TX, TY, FLOW, S, R>(C, P, blockIdx.x * TX, blockIdx.y * TY, smem);
 }
-template <int TX, int TY, bool FLOW, class S>
+template <int TX, int TY, bool FLOW, class S, int R>
 __global__ std::enable_if_t<Storage<S>::DEV> __launch_bounds__(TX* TY)
     step_kernel(const Consts C, const StepPtrs P) {
   extern __shared__ float smem[];
-  step_tile<TX, TY, FLOW, S>(C, P, blockIdx.x * TX, blockIdx.y * TY, smem);
+  step_tile<TX, TY, FLOW, S, R>(C, P, blockIdx.x * TX, blockIdx.y * TY, smem);
 }
 
 // ---- many grids in one launch ----------------------------------------------------------

@@ -55,6 +55,7 @@ class Params(ctypes.Structure):
         ("U_in", ctypes.c_double), ("u_in", ctypes.c_double), ("nu", ctypes.c_double),
         ("bc", ctypes.c_int32 * 4), ("flow", ctypes.c_int32),
         ("check_every", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("stencil", ctypes.c_int32), ("fold", ctypes.c_int32),
     ]
 
 
@@ -114,7 +115,8 @@ def _check(rc: int, what: str):
 
 def make_params(nx, ny, *, dx=0.4, dt=0.008, W0=1.0, tau0=1.0, D=2.0, lam=0.0, L_sat=1.0,
                 eps=0.05, kappa_N=1.0, U_in=0.0, u_in=0.0, nu=0.016,
-                bc=(BC_PERIODIC,) * 4, flow=False, check_every=0, storage="f32") -> Params:
+                bc=(BC_PERIODIC,) * 4, flow=False, check_every=0, storage="f32", stencil=4,
+                fold=6) -> Params:
     p = Params()
     _check(lib().lbmice_params_default(ctypes.byref(p), int(nx), int(ny)), "params_default")
     p.dx, p.dt, p.W0, p.tau0 = dx, dt, W0, tau0
@@ -125,6 +127,7 @@ def make_params(nx, ny, *, dx=0.4, dt=0.008, W0=1.0, tau0=1.0, D=2.0, lam=0.0, L
     p.flow = 1 if flow else 0
     p.check_every = int(check_every)
     p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    p.stencil, p.fold = int(stencil), int(fold)
     return p
 
 

@@ -42,6 +42,8 @@ class Workload:
     nu: float = 0.016
     bc: tuple = (BC_PERIODIC,) * 4
     flow: bool = False
+    stencil: int = 4  # gradient stencil (Sec. 3.1.1): 2, 4, 6, 8
+    fold: int = 6     # anisotropy symmetry: 6 (ice) or 4 (the validation case)
     # seed
     cx: float = 0.0
     cy: float = 0.0
@@ -52,7 +54,7 @@ class Workload:
         return dict(dx=self.dx, dt=self.dt, W0=self.W0, tau0=self.tau0, D=self.D,
                     lam=self.lam, L_sat=self.L_sat, eps=self.eps, kappa_N=self.kappa_N,
                     U_in=self.U_in, u_in=self.u_in, nu=self.nu, bc=tuple(self.bc),
-                    flow=self.flow)
+                    flow=self.flow, stencil=self.stencil, fold=self.fold)
 
     def with_size(self, nx: int, ny: int, **kw) -> "Workload":
         """The same physics on another grid, the seed kept at the same relative place."""
@@ -82,7 +84,34 @@ C2 = Workload("ventilated_512x384", 512, 384, 20000, D=2.0, eps=0.05, U0=0.3, U_
 C3 = Workload("plate_periodic_2048x2048", 2048, 2048, 50000, D=3.0, eps=0.05, U0=0.5,
               flow=True, cx=1024, cy=1024, R0=10.0)
 
-WORKLOADS = {w.name: w for w in (C1, C2, C3)}
+# ---- method variants and the paper's other parameter sets (units W0 = tau0 = 1) ------------
+# Table 2 (Sec. 3.2): plate-regime morphologies on 400 x 400 with W0 = 1.25 dx, tau0 = 20 dt
+# (dx = 0.8, dt = 0.05), eps = 0.05, lambda = 3, D from the beta = 0 relation
+# D = a2 lambda W0^2 / tau0; U0 and L_sat per morphology, seed R0 = 10 at the centre.
+A2 = 0.6267
+TABLE2 = [("solid_plate", 0.4, 2.0), ("stellar_plate_I", 0.5, 1.8), ("sectored_plate", 0.5, 1.6),
+          ("stars", 0.6, 1.0), ("fern_dendrite", 0.8, 1.6), ("fernlike_stellar", 0.7, 1.6),
+          ("stellar_plate_II", 0.5, 1.2)]
+TABLE2_WORKLOADS = [
+    Workload(f"table2_{i + 1}_{name}_400x400", 400, 400, 20000, dx=0.8, dt=0.05, lam=3.0,
+             D=A2 * 3.0, eps=0.05, U0=U0, L_sat=L_sat, cx=200, cy=200, R0=10.0)
+    for i, (name, U0, L_sat) in enumerate(TABLE2)]
+# Four-fold validation system (Sec. 3.1.2): dx = 0.4, dt = 0.008, D = 4, lambda = 6.3826
+# (beta = 0), eps = 0.05 with cos(4 theta), seed R0 = 10 at the centre; U0 = 0.3 on 1000^2,
+# U0 = 0.55 on 500^2.
+FOURFOLD_030 = Workload("fourfold_U030_1000x1000", 1000, 1000, 130000, D=4.0, eps=0.05, U0=0.3,
+                        fold=4, cx=500, cy=500, R0=10.0)
+FOURFOLD_055 = Workload("fourfold_U055_500x500", 500, 500, 50000, D=4.0, eps=0.05, U0=0.55,
+                        fold=4, cx=250, cy=250, R0=10.0)
+# Gradient-isotropy system (Sec. 3.1.1): 800^2, dx/W0 = 0.8, dt/tau0 = 0.096, D = 1 (W0^2/tau0),
+# lambda = 10, eps = 0.05 six-fold, driving U0 = 0.3 (the undercooling 0.3), seed R0 = 10 at the
+# centre, 10^5 steps; one workload per stencil.
+ISOTROPY = {s: Workload(f"isotropy_E{s}_800x800", 800, 800, 100000, dx=0.8, dt=0.096, D=1.0,
+                        lam=10.0, eps=0.05, U0=0.3, cx=400, cy=400, R0=10.0, stencil=s)
+            for s in (2, 4, 6, 8)}
+
+WORKLOADS = {w.name: w for w in (C1, C2, C3, FOURFOLD_030, FOURFOLD_055, *TABLE2_WORKLOADS,
+                                 *ISOTROPY.values())}
 
 
 def seed_fields(w: Workload) -> dict:

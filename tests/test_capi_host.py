@@ -69,6 +69,8 @@ def test_params_default_and_strerror(L):
     (dict(flow=True, u_in=0.6, bc=(1, 2, 3, 3)), lbmice.EUNSTABLE),
     (dict(check_every=-1), lbmice.EINVAL),
     (dict(storage=3), lbmice.EINVAL),
+    (dict(stencil=3), lbmice.EINVAL),
+    (dict(fold=5), lbmice.EINVAL),
 ])
 def test_create_rejects_bad_parameters_without_a_gpu(L, change, code):
     kw = dict(nx=16, ny=16)
