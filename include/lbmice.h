@@ -216,7 +216,9 @@ typedef struct lbmice_batch lbmice_batch_t;
 #define LBMICE_BATCH_MAX_PER_LAUNCH 128
 
 /* Create count member grids from params[0..count-1] on stream (as lbmice_create each), all
- * with tile shape 32x8. Errors: EINVAL (count < 1, null, mixed flow or storage, any member's
+ * with tile shape 32x8. The batched tile is the default scheme only: every member takes the
+ * E4 gradient and the six-fold anisotropy (stencil 0 or 4, fold 0 or 6). Errors: EINVAL
+ * (count < 1, null, mixed flow or storage, another stencil or fold, any member's
  * parameters), EUNSTABLE, ENOMEM, ECUDA; nothing is leaked on error. */
 int lbmice_batch_create(const lbmice_params* params, int32_t count, void* stream,
                         lbmice_batch_t** out);

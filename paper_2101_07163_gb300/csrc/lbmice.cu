@@ -182,9 +182,10 @@ int launch_step_ptrs(const lbmice_t* h, const StepPtrs& P, cudaStream_t st) {
       return cuda_err(cudaGetLastError());
     });
   };
-  // E6 and E8 reach two nodes out: their kernels hold a phi halo of 3
-  return h->C.stencil >= 6 ? launch(std::integral_constant<int, 2>{})
-                           : launch(std::integral_constant<int, 1>{});
+  // The default (E4, six-fold) runs on the specialised radius-1 tile; every other stencil
+  // and fold on the general tile of radius 2 (E6 and E8 reach two nodes out: phi halo 3)
+  return h->C.stencil == 4 && h->C.fold == 6 ? launch(std::integral_constant<int, 1>{})
+                                             : launch(std::integral_constant<int, 2>{});
 }
 
 // Step s of grid h on its own rotating buffers.
@@ -801,7 +802,10 @@ int lbmice_batch_create(const lbmice_params* params, int32_t count, void* stream
   for (int i = 0; i < count; ++i) {
     if (params[i].flow != params[0].flow || params[i].storage != params[0].storage)
       return LBMICE_EINVAL;
-    if (params[i].stencil == 6 || params[i].stencil == 8) return LBMICE_EINVAL;
+    // the batched tile is the default one: E4 gradient, six-fold anisotropy
+    if ((params[i].stencil != 0 && params[i].stencil != 4) ||
+        (params[i].fold != 0 && params[i].fold != 6))
+      return LBMICE_EINVAL;
     const int rc = validate(params[i]);
     if (rc != LBMICE_OK) return rc;
   }

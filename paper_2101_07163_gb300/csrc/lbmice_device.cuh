@@ -272,41 +272,52 @@ __device__ __forceinline__ void aniso(T gx, T gy, T eps, T kNkeps, int fold, T& 
   }
 }
 
+// Round-to-nearest product and fused multiply-add for float and double: the compiler never
+// contracts or reassociates them, so every kernel computing the same expression gets the
+// same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return fma(a, b, c); }
+
 // Isotropic gradient with the stencil of the run (Sec. 3.1.1): E2 is the central difference;
 // E4, E6, E8 sum w(|c|^2) phi(x + c) c over the neighbour shells of Table 1 with the printed
 // weights (they carry the 1/c_s^2). P(dx, dy) is phi at the offset. Every shell is a sum of
 // differences of opposite neighbours, grouped so that mirrored fields give exactly mirrored
-// gradients; E4 is written exactly as the kernels always computed it.
+// gradients, and every product is explicitly rounded.
 template <class T, class F>
 __device__ __forceinline__ void gradient_stencil(int stencil, F P, T& gx, T& gy) {
   if (stencil == 2) {
-    gx = T(0.5) * (P(1, 0) - P(-1, 0));
-    gy = T(0.5) * (P(0, 1) - P(0, -1));
+    gx = mul_rn(T(0.5), P(1, 0) - P(-1, 0));
+    gy = mul_rn(T(0.5), P(0, 1) - P(0, -1));
     return;
   }
   if (stencil == 4) {
-    gx = T(1.0 / 3.0) * (P(1, 0) - P(-1, 0)) +
-         T(1.0 / 12.0) * ((P(1, 1) - P(-1, 1)) + (P(1, -1) - P(-1, -1)));
-    gy = T(1.0 / 3.0) * (P(0, 1) - P(0, -1)) +
-         T(1.0 / 12.0) * ((P(1, 1) - P(1, -1)) + (P(-1, 1) - P(-1, -1)));
+    gx = fma_rn(T(1.0 / 3.0), P(1, 0) - P(-1, 0),
+                mul_rn(T(1.0 / 12.0), (P(1, 1) - P(-1, 1)) + (P(1, -1) - P(-1, -1))));
+    gy = fma_rn(T(1.0 / 3.0), P(0, 1) - P(0, -1),
+                mul_rn(T(1.0 / 12.0), (P(1, 1) - P(1, -1)) + (P(-1, 1) - P(-1, -1))));
     return;
   }
   const bool e8 = stencil == 8;
   const T w1 = e8 ? T(4.0 / 21.0) : T(4.0 / 15.0);
   const T w2 = e8 ? T(4.0 / 45.0) : T(1.0 / 10.0);
   const T w4x2 = e8 ? T(2.0 / 60.0) : T(2.0 / 120.0);
-  T ax = w1 * (P(1, 0) - P(-1, 0)) + w2 * ((P(1, 1) - P(-1, 1)) + (P(1, -1) - P(-1, -1)));
-  T ay = w1 * (P(0, 1) - P(0, -1)) + w2 * ((P(1, 1) - P(1, -1)) + (P(-1, 1) - P(-1, -1)));
-  ax = ax + w4x2 * (P(2, 0) - P(-2, 0));
-  ay = ay + w4x2 * (P(0, 2) - P(0, -2));
+  T ax = fma_rn(w1, P(1, 0) - P(-1, 0), mul_rn(w2, (P(1, 1) - P(-1, 1)) + (P(1, -1) - P(-1, -1))));
+  T ay = fma_rn(w1, P(0, 1) - P(0, -1), mul_rn(w2, (P(1, 1) - P(1, -1)) + (P(-1, 1) - P(-1, -1))));
+  ax = fma_rn(w4x2, P(2, 0) - P(-2, 0), ax);
+  ay = fma_rn(w4x2, P(0, 2) - P(0, -2), ay);
   if (e8) {
     const T w5 = T(2.0 / 315.0), w8x2 = T(2.0 / 5040.0);
-    ax = ax + w5 * (((P(1, 2) - P(-1, 2)) + (P(1, -2) - P(-1, -2))) +
-                    T(2) * ((P(2, 1) - P(-2, 1)) + (P(2, -1) - P(-2, -1))));
-    ay = ay + w5 * (T(2) * ((P(1, 2) - P(1, -2)) + (P(-1, 2) - P(-1, -2))) +
-                    ((P(2, 1) - P(2, -1)) + (P(-2, 1) - P(-2, -1))));
-    ax = ax + w8x2 * ((P(2, 2) - P(-2, 2)) + (P(2, -2) - P(-2, -2)));
-    ay = ay + w8x2 * ((P(2, 2) - P(2, -2)) + (P(-2, 2) - P(-2, -2)));
+    // |c|^2 = 5 shell: (1, 2) and (2, 1) families; the factor 2 is exact
+    const T dx5 = fma_rn(T(2), (P(2, 1) - P(-2, 1)) + (P(2, -1) - P(-2, -1)),
+                         (P(1, 2) - P(-1, 2)) + (P(1, -2) - P(-1, -2)));
+    const T dy5 = fma_rn(T(2), (P(1, 2) - P(1, -2)) + (P(-1, 2) - P(-1, -2)),
+                         (P(2, 1) - P(2, -1)) + (P(-2, 1) - P(-2, -1)));
+    ax = fma_rn(w5, dx5, ax);
+    ay = fma_rn(w5, dy5, ay);
+    ax = fma_rn(w8x2, (P(2, 2) - P(-2, 2)) + (P(2, -2) - P(-2, -2)), ax);
+    ay = fma_rn(w8x2, (P(2, 2) - P(2, -2)) + (P(-2, 2) - P(-2, -2)), ay);
   }
   gx = ax;
   gy = ay;

@@ -34,9 +34,10 @@ struct StepPtrs {
   float* __restrict__ rho_np1;
 };
 
-// Tile of TX x TY destination nodes for a gradient stencil of radius R (1: E2/E4, 2: E6/E8):
-// the phi tile has a halo of R + 1 (the stencil around every ring node), the collided source
-// tile a halo of 1.
+// Tile of TX x TY destination nodes for a gradient stencil of radius R (1: the default E4
+// with six-fold anisotropy, specialised; 2: any stencil up to E8 and either fold): the phi
+// tile has a halo of R + 1 (the stencil around every ring node), the collided source tile a
+// halo of 1.
 template <int TX, int TY, int R = 1>
 struct Tile {
   static constexpr int H = R + 1;
@@ -201,58 +202,66 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
 
   // ---- gradient of phi (Sec. 3.1.1, Table 1) and anisotropy (Sec. 2.1) ----
   float gx, gy;
-  if (R == 1 && C.stencil != 2) {  // E4 (the default)
+  if (R == 1) {  // E4 with six-fold anisotropy: the default, with no run-time variant branch
     const float pE = sphi[pc + 1], pW = sphi[pc - 1];
     const float pN = sphi[pc + T::PW], pS = sphi[pc - T::PW];
     const float pNE = sphi[pc + T::PW + 1], pNW = sphi[pc + T::PW - 1];
     const float pSE = sphi[pc - T::PW + 1], pSW = sphi[pc - T::PW - 1];
-    gx = kW1 * (pE - pW) + kW2 * ((pNE - pNW) + (pSE - pSW));
-    gy = kW1 * (pN - pS) + kW2 * ((pNE - pSE) + (pNW - pSW));
-  } else {  // E2, or E6 / E8 on a tile of halo R + 1 = 3
+    gx = fmaf(kW1, pE - pW, __fmul_rn(kW2, (pNE - pNW) + (pSE - pSW)));
+    gy = fmaf(kW1, pN - pS, __fmul_rn(kW2, (pNE - pSE) + (pNW - pSW)));
+  } else {  // any stencil and fold, chosen at run time, on a phi tile of halo R + 1 = 3
     gradient_stencil<float>(C.stencil, [&](int dx, int dy) { return sphi[pc + dy * T::PW + dx]; },
                             gx, gy);
   }
+  // Every product and sum from here to the collision is an explicit fmaf or round-to-nearest
+  // operation, like the collision itself: no kernel that collides a node may contract them
+  // differently, so single-grid and batched kernels give the same bits.
   float as = 1.0f, Nx = 0.0f, Ny = 0.0f;
   {
-    const float s2 = gx * gx + gy * gy;
+    const float s2 = fmaf(gx, gx, __fmul_rn(gy, gy));
     if (s2 > 1e-12f) {  // |grad phi|^2 <= 1e-12: isotropic, no anisotropic flux
       const float rinv = rsqrtf(s2);
-      const float nx = gx * rinv, ny = gy * rinv;
-      const float X2 = nx * nx, Y2 = ny * ny;
+      const float nx = __fmul_rn(gx, rinv), ny = __fmul_rn(gy, rinv);
+      const float X2 = __fmul_rn(nx, nx), Y2 = __fmul_rn(ny, ny);
+      const float XX = __fmul_rn(X2, X2), YY = __fmul_rn(Y2, Y2), XY = __fmul_rn(X2, Y2);
+      const float nxny = __fmul_rn(nx, ny);
       float cosk, sink;
-      if (C.fold == 4) {  // the four-fold validation case: cos/sin(4 theta)
-        cosk = X2 * X2 - 6.0f * X2 * Y2 + Y2 * Y2;
-        sink = 4.0f * nx * ny * (X2 - Y2);
+      if (R != 1 && C.fold == 4) {  // the four-fold validation case: cos/sin(4 theta)
+        cosk = fmaf(-6.0f, XY, XX + YY);                       // X^2 - 6XY + Y^2
+        sink = __fmul_rn(__fmul_rn(4.0f, nxny), X2 - Y2);      // 4 nx ny (X - Y)
       } else {  // six-fold (ice): cos/sin(6 theta)
-        cosk = X2 * X2 * X2 - 15.0f * X2 * X2 * Y2 + 15.0f * X2 * Y2 * Y2 - Y2 * Y2 * Y2;
-        sink = nx * ny * (6.0f * X2 * X2 - 20.0f * X2 * Y2 + 6.0f * Y2 * Y2);
+        cosk = __fmul_rn(X2 - Y2, fmaf(-14.0f, XY, XX + YY));  // X^3 - 15X^2Y + 15XY^2 - Y^3
+        sink = __fmul_rn(nxny, fmaf(-20.0f, XY, __fmul_rn(6.0f, XX + YY)));
       }
-      as = 1.0f + C.eps * cosk;
-      const float t = C.kNkeps * as * sink;
-      Nx = t * gy;
-      Ny = -(t * gx);
+      as = fmaf(C.eps, cosk, 1.0f);
+      const float t = __fmul_rn(__fmul_rn(C.kNkeps, as), sink);
+      Nx = __fmul_rn(t, gy);
+      Ny = -__fmul_rn(t, gx);
     }
   }
-  const float as2 = as * as;
+  const float as2 = __fmul_rn(as, as);
   const float inv_as2 = __fdividef(1.0f, as2);
-  const float inv_eta = __fdividef(1.0f, C.Dphi3 * as2 + 0.5f);
-  const float omp2 = 1.0f - ph * ph;
-  const float srcQ = (ph - ph * ph * ph + C.lambda * U * omp2 * omp2) * C.dt_tau0;
+  const float inv_eta = __fdividef(1.0f, fmaf(C.Dphi3, as2, 0.5f));
+  const float omp2 = fmaf(-ph, ph, 1.0f);
+  const float srcQ =
+      __fmul_rn((ph - __fmul_rn(__fmul_rn(ph, ph), ph)) +
+                    __fmul_rn(__fmul_rn(C.lambda, U), __fmul_rn(omp2, omp2)),
+                C.dt_tau0);
 
   // ---- flow velocity with solid damping (Sec. 2.2.1) ----
   float usx = 0.0f, usy = 0.0f, k = 0.0f;
   if (FLOW) {
     const float onep = 1.0f + ph;
-    k = C.kdrag * rho * onep * onep * (1.0f - ph);
-    const float inv = __fdividef(1.0f, rho + 0.5f * k);
-    const float sfac = 0.5f * (1.0f - ph);
-    usx = sfac * (jx * inv);
-    usy = sfac * (jy * inv);
+    k = __fmul_rn(__fmul_rn(__fmul_rn(C.kdrag, rho), __fmul_rn(onep, onep)), 1.0f - ph);
+    const float inv = __fdividef(1.0f, fmaf(0.5f, k, rho));
+    const float sfac = __fmul_rn(0.5f, 1.0f - ph);
+    usx = __fmul_rn(sfac, __fmul_rn(jx, inv));
+    usy = __fmul_rn(sfac, __fmul_rn(jy, inv));
   }
   // ---- vapour relaxation and source (Sec. 2.2.2) ----
   const float q = fminf(fmaxf(1.0f - ph, 0.0f), 2.0f);
-  const float inv_tg = __fdividef(1.0f, C.Dlat3 * q + 0.5f);
-  const float srcU = -C.half_Lsat * (ph - php);
+  const float inv_tg = __fdividef(1.0f, fmaf(C.Dlat3, q, 0.5f));
+  const float srcU = __fmul_rn(-C.half_Lsat, ph - php);
 
   if (OWN) {
 #pragma unroll

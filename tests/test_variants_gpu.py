@@ -60,10 +60,12 @@ def test_mirror_symmetry_with_every_stencil_on_gpu(stencil):
 
 
 def test_wide_stencils_and_four_fold_are_refused_where_not_built():
-    w6 = W.Workload("b", 40, 40, 1, flow=True, stencil=6)
-    with pytest.raises(lbmice.LbmiceError) as ei:
-        lbmice.Batch([dict(nx=40, ny=40, **w6.params())])
-    assert ei.value.code == lbmice.EINVAL
+    for kw in (dict(stencil=2), dict(stencil=6), dict(stencil=8), dict(fold=4)):
+        wb = W.Workload("b", 40, 40, 1, flow=True, **kw)
+        with pytest.raises(lbmice.LbmiceError) as ei:
+            lbmice.Batch([dict(nx=40, ny=40, **W.Workload("a", 40, 40, 1, flow=True).params()),
+                          dict(nx=40, ny=40, **wb.params())])
+        assert ei.value.code == lbmice.EINVAL
     for kw in (dict(stencil=2), dict(stencil=8), dict(fold=4)):
         w = W.Workload("t", 40, 40, 1, flow=True, **kw)
         lat = lbmice.Lattice(w.nx, w.ny, **w.params())
