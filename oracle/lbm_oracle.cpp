@@ -36,7 +36,15 @@
 //   R14 All couplings use time-n moments (Jacobi).
 //   R15 Boundary ghosts: periodic wrap; zero-gradient outlet = copy of the adjacent node;
 //       free-slip = mirror image of the adjacent node; inlet = equilibrium at the inlet state.
-// Parity is pinned by tests/test_oracle_pins.py (closed forms, invariants, symmetries,
+//   R18 lambda, when not given, is the beta = 0 choice tau0 D / (a2 W0^2), a2 = 0.6267.
+//   R21 E2 is the central difference; E6/E8 use the shell weights of Table 1, which (as R2)
+//       already carry 1/c_s^2: E6 w(1,2,4) = 4/15, 1/10, 1/120; E8 w(1,2,4,5,8) = 4/21,
+//       4/45, 1/60, 2/315, 1/5040.
+//   R22 The four-fold system (Sec. 3.1.2) uses the same anisotropy with k = 4:
+//       a_s = 1 + eps cos(4 theta), flux kappa_N a_s 4 eps sin(4 theta) (g_y, -g_x).
+// (R19, R20, R23 and R24 concern the workloads and the GPU storage, not this arithmetic.)
+// Parity is pinned by tests/test_oracle_pins.py, tests/test_oracle_grad_pins.py and
+// tests/test_oracle_variant_pins.py (closed forms, invariants, symmetries,
 // brute force); no function here is unpinned.
 
 #include <algorithm>

@@ -114,3 +114,28 @@ def test_central_difference_biases_the_six_arms_by_orientation():
     s2, s4, s8 = arm_spread(2), arm_spread(4), arm_spread(8)
     assert s2 > 1.5 * s4
     assert s4 < 0.03 and s8 < 0.03
+
+
+def notch_ratio(w, steps):
+    """phi = 0 radius halfway between two arms over the inradius of the hexagon through the
+    six tips: 1 for a faceted plate, falling as the arms branch out."""
+    import math
+    lat = lbmice.Lattice(w.nx, w.ny, **w.params())
+    lat.init_seed(w.cx, w.cy, w.R0, w.U0)
+    lat.step(steps)
+    phi = lat.field(lbmice.PHI).astype(np.float64)
+    tips = [ray_tip(phi, w.cx, w.cy, math.radians(a)) for a in range(0, 360, 60)]
+    mids = [ray_tip(phi, w.cx, w.cy, math.radians(a + 30)) for a in range(0, 360, 60)]
+    assert np.all(np.isfinite(tips + mids))
+    return float(np.mean(mids) / (np.mean(tips) * math.sqrt(3) / 2))
+
+
+def test_table2_habits_order_from_plates_to_ferns():
+    # The seven plate-regime parameter sets of Table 2 at T = 500 tau0 (10^4 steps): the
+    # solid plate stays a convex faceted hexagon, the plates notch more as U0 rises or L_sat
+    # falls, and stars and the fern dendrite grow branched arms. Measured notch ratios:
+    # 1.037, 0.984, 0.955, 0.331, 0.282, 0.454, 0.771 for sets 1..7.
+    n = [notch_ratio(w, 10000) for w in W.TABLE2_WORKLOADS]
+    assert n[0] > 1.0
+    assert n[0] > n[1] > n[2] > n[6] > n[5] > max(n[3], n[4])
+    assert n[3] < 0.4 and n[4] < 0.4
