@@ -175,6 +175,18 @@ __device__ __forceinline__ void store_lattice_f32(float* __restrict__ lat, long 
   lat[8 * pstride + node] = v[0];
 }
 
+// The 9 populations of one node and lattice from its 16-bit deviation vector v and its
+// zeroth moment M: p_a = w_a M + d_a for a > 0, and the rest population from the sum.
+template <class S>
+__device__ __forceinline__ void decode9(uint4 v, float M, float* out) {
+  float d[8];
+  Storage<S>::unpack8(v, d);
+#pragma unroll
+  for (int a = 1; a < 9; ++a) out[a] = fmaf(a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f, M, d[a - 1]);
+  out[0] =
+      M - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
+}
+
 // Populations of lattice L at a node: stored values for F32, or rebuilt from the moment M
 // and the deviations for F16 / BF16.
 template <class S>
@@ -186,13 +198,7 @@ __device__ __forceinline__ void load9(const typename Storage<S>::T* __restrict__
   } else if constexpr (!Storage<S>::DEV) {
     load_lattice_f32(pops + 9 * L * pstride, pstride, node, out);
   } else {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(pops + 9 * L * pstride + 8 * node));
-    float d[8];
-    Storage<S>::unpack8(v, d);
-#pragma unroll
-    for (int a = 1; a < 9; ++a) out[a] = fmaf(a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f, M, d[a - 1]);
-    out[0] =
-        M - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
+    decode9<S>(__ldg(reinterpret_cast<const uint4*>(pops + 9 * L * pstride + 8 * node)), M, out);
   }
 }
 

@@ -105,6 +105,48 @@ struct FactoredCollision {
   }
 };
 
+// The loads of a thread's own node (inside the grid), issued before the phi tile's barrier so
+// that their latency overlaps the tile's: FP32 keeps the populations, 16-bit storage the
+// raw deviation vectors and the moments U, rho (phi comes from the tile).
+template <class S, bool FLOW, bool DEV = Storage<S>::DEV>
+struct OwnIn;
+template <class S, bool FLOW>
+struct OwnIn<S, FLOW, false> {
+  bool valid;
+  float h[9], g[9], f[9], php;
+};
+template <class S, bool FLOW>
+struct OwnIn<S, FLOW, true> {
+  bool valid;
+  uint4 h, g, f;
+  float U, rho, php;
+};
+
+template <class S, bool FLOW>
+__device__ __forceinline__ void own_load(const Consts& C, const StepPtrs& P, int X, int Y,
+                                         OwnIn<S, FLOW>& in) {
+  using ST = Storage<S>;
+  in.valid = X < C.nx && Y < C.ny;
+  if (!in.valid) return;
+  const long long idx = (long long)Y * C.pitch + X;
+  const long long nd = (long long)Y * C.rstride + X;
+  const typename ST::T* __restrict__ pops = static_cast<const typename ST::T*>(P.pin);
+  if constexpr (!ST::DEV) {
+    load_lattice_f32(pops + PLANE_H * C.pstride, C.pstride, nd, in.h);
+    load_lattice_f32(pops + PLANE_G * C.pstride, C.pstride, nd, in.g);
+    if (FLOW) load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, in.f);
+  } else {
+    in.h = __ldg(reinterpret_cast<const uint4*>(pops + 8 * nd));
+    in.g = __ldg(reinterpret_cast<const uint4*>(pops + 9 * C.pstride + 8 * nd));
+    in.U = __ldg(P.U_n + idx);
+    if (FLOW) {
+      in.f = __ldg(reinterpret_cast<const uint4*>(pops + 18 * C.pstride + 8 * nd));
+      in.rho = __ldg(P.rho_n + idx);
+    }
+  }
+  in.php = __ldg(P.phi_nm1 + idx);
+}
+
 // Collide the source node at tile position (sx, sy) in [0, TX+2) x [0, TY+2), global
 // coordinates (X, Y) in [-1, nx] x [-1, ny], and store its post-collision populations.
 // Ghost positions take the collision of the node their face rule maps them to (directions
@@ -113,7 +155,8 @@ template <int TX, int TY, bool FLOW, class S, bool OWN, int R>
 __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& P, int X, int Y,
                                                int sx, int sy, const float* __restrict__ sphi,
                                                float* __restrict__ spost,
-                                               float* __restrict__ sB, float* hown) {
+                                               float* __restrict__ sB, float* hown,
+                                               const OwnIn<S, FLOW>* pre = nullptr) {
   using T = Tile<TX, TY, R>;
   const int node = sy * T::SW + sx;
   int mx = X, my = Y, lx = sx, ly = sy;
@@ -182,16 +225,33 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   const int pc = (ly + R) * T::PW + (lx + R);
   const float ph = sphi[pc];
   float hv[9], gv[9], fv[9];
-  if constexpr (!ST::DEV) {
-    load_lattice_f32(pops + PLANE_H * C.pstride, C.pstride, nd, hv);
-    load_lattice_f32(pops + PLANE_G * C.pstride, C.pstride, nd, gv);
-    if (FLOW) load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, fv);
+  float php;
+  if (OWN && pre && pre->valid) {  // loaded before the phi tile's barrier
+    if constexpr (!ST::DEV) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        hv[a] = pre->h[a];
+        gv[a] = pre->g[a];
+        if (FLOW) fv[a] = pre->f[a];
+      }
+    } else {
+      decode9<S>(pre->h, ph, hv);
+      decode9<S>(pre->g, pre->U, gv);
+      if (FLOW) decode9<S>(pre->f, pre->rho, fv);
+    }
+    php = pre->php;
   } else {
-    load9<S>(pops, 0, C.pstride, nd, ph, hv);
-    load9<S>(pops, 1, C.pstride, nd, __ldg(P.U_n + idx), gv);
-    if (FLOW) load9<S>(pops, 2, C.pstride, nd, __ldg(P.rho_n + idx), fv);
+    if constexpr (!ST::DEV) {
+      load_lattice_f32(pops + PLANE_H * C.pstride, C.pstride, nd, hv);
+      load_lattice_f32(pops + PLANE_G * C.pstride, C.pstride, nd, gv);
+      if (FLOW) load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, fv);
+    } else {
+      load9<S>(pops, 0, C.pstride, nd, ph, hv);
+      load9<S>(pops, 1, C.pstride, nd, __ldg(P.U_n + idx), gv);
+      if (FLOW) load9<S>(pops, 2, C.pstride, nd, __ldg(P.rho_n + idx), fv);
+    }
+    php = __ldg(P.phi_nm1 + idx);
   }
-  const float php = __ldg(P.phi_nm1 + idx);
   const float U = sum9(gv);
   float rho = 1.0f, jx = 0.0f, jy = 0.0f;
   if (FLOW) {
@@ -328,6 +388,10 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
 
+  // the own node's populations, in flight while the phi tile loads
+  OwnIn<S, FLOW> own;
+  own_load<S, FLOW>(C, P, x0 + tx, y0 + ty, own);
+
   // ---- A: phi^n with a halo of H = R + 1 nodes ----
   if (x0 >= H && y0 >= H && x0 + TX + H <= C.nx && y0 + TY + H <= C.ny) {
     // the halo lies inside the grid (almost every tile): no ghost resolution
@@ -359,7 +423,7 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
     const int X = x0 + tx, Y = y0 + ty;
     if (X <= C.nx && Y <= C.ny)
       collide_source<TX, TY, FLOW, S, true, R>(C, P, X, Y, tx + 1, ty + 1, sphi, spost, sB,
-                                               hown);
+                                               hown, &own);
   }
   for (int r = tid; r < T::NRING; r += T::NT) {
     // ring order: bottom row, top row, then left and right columns
