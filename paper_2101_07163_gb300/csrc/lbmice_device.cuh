@@ -187,6 +187,14 @@ __device__ __forceinline__ void decode9(uint4 v, float M, float* out) {
       M - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
 }
 
+// The 9 deviations d_a = p_a - w_a M of one node and lattice from its 16-bit vector v; the
+// rest one is d_0 = -sum_{a>0} d_a, since the populations sum to M.
+template <class S>
+__device__ __forceinline__ void deviations9(uint4 v, float* d) {
+  Storage<S>::unpack8(v, d + 1);
+  d[0] = -(((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8])));
+}
+
 // Populations of lattice L at a node: stored values for F32, or rebuilt from the moment M
 // and the deviations for F16 / BF16.
 template <class S>

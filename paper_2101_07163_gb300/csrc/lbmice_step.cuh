@@ -92,6 +92,14 @@ struct FactoredCollision {
       c6 = __fmul_rn(9.0f, C.guo);
     }
   }
+  // Populations given as deviations d_a = p_a - w_a M from the moments (phi, U, rho): each
+  // collision is affine in p_a with slope a1, b1 or c1, so adding slope x M to the constant
+  // term gives the same collided populations from the deviations.
+  __device__ __forceinline__ void shift(float Mh, float Mg, float Mf) {
+    a2 = fmaf(a1, Mh, a2);
+    b2 = fmaf(b1, Mg, b2);
+    if (FLOW) c2 = fmaf(c1, Mf, c2);
+  }
   __device__ __forceinline__ float h(int a, float hv, float Nx, float Ny) const {
     return fmaf(hv, a1, __fmul_rn(w_of(a), fmaf(-a3, cdot(a, Nx, Ny), a2)));
   }
@@ -224,8 +232,11 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   // ---- populations and moments at time n (Sec. 2.2) ----
   const int pc = (ly + R) * T::PW + (lx + R);
   const float ph = sphi[pc];
+  // FP32: the populations. 16-bit: their deviations d_a = p_a - w_a M from the stored
+  // moments M (phi, U, rho), with d_0 = -sum_{a>0} d_a; the moments are the stored ones and
+  // the momentum is sum c_a d_a (the w_a M terms cancel exactly).
   float hv[9], gv[9], fv[9];
-  float php;
+  float php, U, rho = 1.0f;
   if (OWN && pre && pre->valid) {  // loaded before the phi tile's barrier
     if constexpr (!ST::DEV) {
 #pragma unroll
@@ -235,9 +246,13 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
         if (FLOW) fv[a] = pre->f[a];
       }
     } else {
-      decode9<S>(pre->h, ph, hv);
-      decode9<S>(pre->g, pre->U, gv);
-      if (FLOW) decode9<S>(pre->f, pre->rho, fv);
+      deviations9<S>(pre->h, hv);
+      deviations9<S>(pre->g, gv);
+      U = pre->U;
+      if (FLOW) {
+        deviations9<S>(pre->f, fv);
+        rho = pre->rho;
+      }
     }
     php = pre->php;
   } else {
@@ -246,16 +261,23 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
       load_lattice_f32(pops + PLANE_G * C.pstride, C.pstride, nd, gv);
       if (FLOW) load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, fv);
     } else {
-      load9<S>(pops, 0, C.pstride, nd, ph, hv);
-      load9<S>(pops, 1, C.pstride, nd, __ldg(P.U_n + idx), gv);
-      if (FLOW) load9<S>(pops, 2, C.pstride, nd, __ldg(P.rho_n + idx), fv);
+      const uint4* pv = reinterpret_cast<const uint4*>(pops);
+      deviations9<S>(__ldg(pv + nd), hv);
+      deviations9<S>(__ldg(pv + (9 * C.pstride) / 8 + nd), gv);
+      U = __ldg(P.U_n + idx);
+      if (FLOW) {
+        deviations9<S>(__ldg(pv + (18 * C.pstride) / 8 + nd), fv);
+        rho = __ldg(P.rho_n + idx);
+      }
     }
     php = __ldg(P.phi_nm1 + idx);
   }
-  const float U = sum9(gv);
-  float rho = 1.0f, jx = 0.0f, jy = 0.0f;
+  if constexpr (!ST::DEV) {
+    U = sum9(gv);
+    if (FLOW) rho = sum9(fv);
+  }
+  float jx = 0.0f, jy = 0.0f;
   if (FLOW) {
-    rho = sum9(fv);
     jx = sumcx9(fv);
     jy = sumcy9(fv);
   }
@@ -323,9 +345,9 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   const float inv_tg = __fdividef(1.0f, fmaf(C.Dlat3, q, 0.5f));
   const float srcU = __fmul_rn(-C.half_Lsat, ph - php);
 
-  if (OWN) {
+  if (OWN) {  // the own node's h populations, for the pull of Eq. (d)
 #pragma unroll
-    for (int a = 0; a < 9; ++a) hown[a] = hv[a];
+    for (int a = 0; a < 9; ++a) hown[a] = ST::DEV ? fmaf(w_of(a), ph, hv[a]) : hv[a];
   }
   if constexpr (!Storage<S>::DEV) {
     // FP32 storage: the factored collision (FactoredCollision), each collided population
@@ -349,8 +371,10 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     };
     if (mirx || miry) emit(std::true_type{}); else emit(std::false_type{});
   } else {
-    // 16-bit storage: the same factored collision, staged in registers, then stored
+    // 16-bit storage: the same factored collision applied to the deviations (its constant
+    // terms shifted by the moments), staged in registers, then stored
     FactoredCollision<FLOW> fc(C, ph, U, rho, inv_as2, inv_eta, srcQ, inv_tg, srcU, k, usx, usy);
+    fc.shift(ph, U, rho);
     float post[27];
   #pragma unroll
     for (int a = 0; a < 9; ++a) {
