@@ -55,15 +55,19 @@ __device__ __forceinline__ int step_to(int v, int c, int n) {
   return c > 0 ? wrap_p(v + 1, n) : (c < 0 ? wrap_m(v - 1, n) : v);
 }
 
-// Sum of v over the block into part[slot * kAdjParams + k] (thread 0 adds, FP64).
-__device__ __forceinline__ void block_accumulate(double* v, double* out) {
+// Sum of v over the block into out[k] (threads 0..kAdjParams-1 add). Each thread holds one
+// node's FP32 terms: a warp sums its 32 in FP32 (a five-level tree, error below 3e-7 of the
+// sum of magnitudes), and only the warp sums and the running total are FP64 -- the FP64
+// pipe of this part retires about one warp instruction per 64 cycles per scheduler, so an
+// FP64 tree per thread would dominate the kernel.
+__device__ __forceinline__ void block_accumulate(const float* v, double* out) {
   __shared__ double red[8][kAdjParams];
 #pragma unroll
   for (int k = 0; k < kAdjParams; ++k) {
-    double s = v[k];
+    float s = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = s;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = (double)s;
   }
   __syncthreads();
   if (threadIdx.x < kAdjParams) {
@@ -78,7 +82,7 @@ template <bool FLOW>
 __global__ void __launch_bounds__(256) adj_collide_kernel(const Consts C, const AdjPtrs A) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-  double part[kAdjParams] = {0.0, 0.0, 0.0, 0.0};
+  float part[kAdjParams] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (x < C.nx && y < C.ny) {
     const long long Q = C.pstride, R = C.rstride, PI = C.pitch;
     const int xp = wrap_p(x + 1, C.nx), xm = wrap_m(x - 1, C.nx);
@@ -145,7 +149,6 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(const Consts C, const 
     const float q = fminf(fmaxf(qraw, 0.0f), 2.0f);
     const float inv_tg = __fdividef(1.0f, C.Dlat3 * q + 0.5f);
     const float Fx = -k * usx, Fy = -k * usy;
-    const float uF = usx * Fx + usy * Fy;
     const float uu = usx * usx + usy * usy;
 
     // ---- adjoints of the pulled values, gathered from the downstream nodes x + c_a ----
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(const Consts C, const 
     // srcQ = (phi - phi^3 + lambda U (1 - phi^2)^2) dt/tau0
     phb += srcQ_b * C.dt_tau0 * (1.0f - 3.0f * ph * ph - 4.0f * C.lambda * U * omp2 * ph);
     Ub += srcQ_b * C.dt_tau0 * C.lambda * omp2 * omp2;
-    part[ADJ_LAMBDA] += (double)(srcQ_b * C.dt_tau0 * U * omp2 * omp2);
+    part[ADJ_LAMBDA] += srcQ_b * C.dt_tau0 * U * omp2 * omp2;
     // anisotropy: N = t (g_y, -g_x), t = kNkeps a_s sin6, a_s = 1 + eps cos6, n = g / |g|
     float gxb = 0.0f, gyb = 0.0f;
     if (aniso_on) {
@@ -200,9 +203,9 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(const Consts C, const 
       gxb -= Nyb * t;
       as_b += tb * C.kNkeps * sin6;
       const float sin6_b = tb * C.kNkeps * as;
-      part[ADJ_KN6EPS] += (double)(tb * as * sin6);
+      part[ADJ_KN6EPS] += tb * as * sin6;
       const float cos6_b = as_b * C.eps;
-      part[ADJ_EPS] += (double)(as_b * cos6);
+      part[ADJ_EPS] += as_b * cos6;
       const float Pp = 6.0f * X2 * X2 - 20.0f * X2 * Y2 + 6.0f * Y2 * Y2;
       const float X2b = cos6_b * (3.0f * X2 * X2 - 30.0f * X2 * Y2 + 15.0f * Y2 * Y2) +
                         sin6_b * nx * ny * (12.0f * X2 - 20.0f * Y2);
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(const Consts C, const 
     const float phpb = C.half_Lsat * srcU_b;
     // inv_tg = 1/(Dlat3 q + 1/2); q = clamp(1 - phi, 0, 2)
     const float qb = -inv_tg_b * C.Dlat3 * inv_tg * inv_tg;
-    part[ADJ_DLAT3] += (double)(-inv_tg_b * q * inv_tg * inv_tg);
+    part[ADJ_DLAT3] += -inv_tg_b * q * inv_tg * inv_tg;
     if (qraw >= 0.0f && qraw <= 2.0f) phb -= qb;
 
     // ---- flow: f*_a = f_a - (f_a - feq_a)/tau_f + force_a ----
@@ -370,7 +373,7 @@ template <bool FLOW>
 __global__ void __launch_bounds__(256) adj_init_kernel(const Consts C, const InitAdjPtrs A) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-  double part[kAdjParams] = {0.0, 0.0, 0.0, 0.0};
+  float part[kAdjParams] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (x < C.nx && y < C.ny) {
     const long long Q = C.pstride, R = C.rstride, PI = C.pitch;
     const long long ip = (long long)y * R + x, iq = (long long)y * PI + x;
@@ -427,9 +430,9 @@ __global__ void __launch_bounds__(256) adj_init_kernel(const Consts C, const Ini
       gxb -= Nyb * t;
       const float as_b = tb * C.kNkeps * sin6;
       const float sin6_b = tb * C.kNkeps * as;
-      part[ADJ_KN6EPS] += (double)(tb * as * sin6);
+      part[ADJ_KN6EPS] += tb * as * sin6;
       const float cos6_b = as_b * C.eps;
-      part[ADJ_EPS] += (double)(as_b * cos6);
+      part[ADJ_EPS] += as_b * cos6;
       const float X2b = cos6_b * (3.0f * X2 * X2 - 30.0f * X2 * Y2 + 15.0f * Y2 * Y2) +
                         sin6_b * nx * ny * (12.0f * X2 - 20.0f * Y2);
       const float Y2b = cos6_b * (-15.0f * X2 * X2 + 30.0f * X2 * Y2 - 3.0f * Y2 * Y2) +
