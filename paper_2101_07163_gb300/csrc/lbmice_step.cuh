@@ -400,7 +400,8 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
 
 // One TX x TY tile with origin (x0, y0), computed by the TX * TY threads of the CTA (thread
 // tid owns node (x0 + tid % TX, y0 + tid / TX)). smem holds Tile<TX, TY, R>::smem_bytes.
-template <int TX, int TY, bool FLOW, class S, int R = 1>
+// PRE: issue the own node's loads before the phi tile's barrier (OwnIn).
+template <int TX, int TY, bool FLOW, class S, int R = 1, bool PRE = true>
 __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, int x0, int y0,
                                           float* smem) {
   using ST = Storage<S>;
@@ -414,7 +415,8 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
 
   // the own node's populations, in flight while the phi tile loads
   OwnIn<S, FLOW> own;
-  own_load<S, FLOW>(C, P, x0 + tx, y0 + ty, own);
+  if (PRE) own_load<S, FLOW>(C, P, x0 + tx, y0 + ty, own);
+  else own.valid = false;
 
   // ---- A: phi^n with a halo of H = R + 1 nodes ----
   if (x0 >= H && y0 >= H && x0 + TX + H <= C.nx && y0 + TY + H <= C.ny) {
@@ -570,7 +572,9 @@ __global__ void __launch_bounds__(TX* TY, 4) batch_step_kernel(const __grid_cons
   const int local = t - L.tile_start[lo];
   const int tyi = local / d.tiles_x, txi = local - tyi * d.tiles_x;
   if (local < 0 || tyi * TY >= d.C.ny) return;
-  step_tile<TX, TY, FLOW, S>(d.C, d.P, txi * TX, tyi * TY, smem);
+  // no own-node preload here: the batched tile is more issue-bound than the single-grid one
+  // and measured 2.7% faster without it
+  step_tile<TX, TY, FLOW, S, 1, false>(d.C, d.P, txi * TX, tyi * TY, smem);
 }
 
 }  // namespace lbmice
