@@ -148,3 +148,32 @@ def test_batch_rejects_mixed_flow_or_storage():
     cf[0]["flow"] = False
     with pytest.raises(lbmice.LbmiceError):
         lbmice.Batch(cf)
+
+
+def test_full_sweep_in_the_benchmark_configuration():
+    # The 96-crystal sweep the benchmark times (35.8 M nodes, 8.2 GB of state), with the tile
+    # shapes its autotuner picks, then one 60-step graph replay and one single launch; one
+    # member of each grid side (inflow along its own axis, inlet/outlet/free-slip faces)
+    # against the FP64 oracle over the same steps.
+    from tests.test_parity_gpu import compare_moments
+    ws = W.batch_sweep()
+    b = lbmice.Batch(configs(ws))
+    for m, w in zip(b.members, ws):
+        m.init_seed(w.cx, w.cy, w.R0, w.U0)
+    shapes, taken = b.autotune(steps_per_trial=2)
+    for m, w in zip(b.members, ws):  # re-seeding every member restarts the batch at step 0
+        m.init_seed(w.cx, w.cy, w.R0, w.U0)
+    b.step(61)
+    picked = {}
+    for i, w in enumerate(ws):
+        picked.setdefault(w.nx, i)
+    assert sorted(picked) == [256, 384, 512, 768, 1024]
+    for n, i in sorted(picked.items()):
+        w = ws[i]
+        o = oracle.Oracle(nx=w.nx, ny=w.ny, **w.params())
+        o.set_fields(**W.seed_fields(w))
+        o.step(61)
+        assert b.members[i].steps_done == 61
+        compare_moments(b.members[i], o, 2e-5)
+        del o
+    b.close()
