@@ -9,8 +9,9 @@ is needed between steps). Prints one JSON line.
 
 --impl reference times the FP64 CPU oracle (the test oracle, as it stands) on the host
 cores, on a band of the same workload per step. Under torchrun with N > 1 every rank runs
-an independent replica of the workload (no data-path collective) and rank 0 reports the
-aggregate over the slowest rank.
+an independent replica of the single-grid workload (no data-path collective) and rank 0
+reports the aggregate over the slowest rank; the batched sweep is sharded by crystal
+instead, its only collective an FP64 sum of the diagnostics after the timed region.
 """
 from __future__ import annotations
 
@@ -99,6 +100,30 @@ def max_over_ranks(dist, value: float) -> float:
 def barrier(dist):
     if dist is not None:
         dist.barrier()
+
+
+def shard_crystals(ws: list, rank: int, world: int) -> list:
+    """The crystals of the batched sweep this rank advances: every world-th member from
+    position rank. The crystals are independent, so the ranks exchange nothing while they
+    step."""
+    return ws[rank::world]
+
+
+STAT_SUMS = ("area", "mass", "vapour_invariant", "nonfinite")
+
+
+def reduce_diagnostics(dist, stats: list) -> dict:
+    """FP64 sums over the crystals of every rank of the per-crystal diagnostics (solid area,
+    mass, vapour invariant, non-finite count): the one collective of the batched leg, after
+    its timed region."""
+    import torch
+    local = [sum(float(st[k]) for st in stats) for k in STAT_SUMS]
+    if dist is not None:
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor(local, dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        local = [float(v) for v in t.tolist()]
+    return dict(zip(STAT_SUMS, local))
 
 
 class ClockSampler:
@@ -244,47 +269,64 @@ def run_reference(args):
     }), flush=True)
 
 
-def run_batched(args, stream, dist):
+def run_batched(args, stream, dist, rank: int = 0, world: int = 1):
     """The 96-crystal batched sweep: autotuned tile shapes, one persistent launch per step
-    (CUDA graphs), against the same members stepped one grid at a time."""
+    (CUDA graphs), against the same members stepped one grid at a time. Under N ranks the
+    crystals are sharded (shard_crystals); the diagnostics are summed over all of them."""
     import torch
     from paper_2101_07163_gb300 import lbmice
-    ws = W.batch_sweep(count=args.batch_count)
-    b = lbmice.Batch([dict(nx=w.nx, ny=w.ny, **w.params()) for w in ws], stream=stream)
-    for m, w in zip(b.members, ws):
-        m.init_seed(w.cx, w.cy, w.R0, w.U0)
-    shapes, _ = b.autotune(steps_per_trial=6)
-    for m, w in zip(b.members, ws):  # restart from the seeds after tuning
-        m.init_seed(w.cx, w.cy, w.R0, w.U0)
-    b.step(12)
-    b.sync()
+    ws_all = W.batch_sweep(count=args.batch_count)
+    ws = shard_crystals(ws_all, rank, world)
     K = args.batch_steps
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b, shapes, ms, ms_seq, launches = None, [], 0.0, 0.0, 0
+    if ws:
+        b = lbmice.Batch([dict(nx=w.nx, ny=w.ny, **w.params()) for w in ws], stream=stream)
+        for m, w in zip(b.members, ws):
+            m.init_seed(w.cx, w.cy, w.R0, w.U0)
+        shapes, _ = b.autotune(steps_per_trial=6)
+        for m, w in zip(b.members, ws):  # restart from the seeds after tuning
+            m.init_seed(w.cx, w.cy, w.R0, w.U0)
+        b.step(12)
+        b.sync()
+        launches = b.launches_per_step
     barrier(dist)
-    e0.record(stream)
-    b.step(K)
-    e1.record(stream)
-    e1.synchronize()
-    ms = max_over_ranks(dist, e0.elapsed_time(e1))
-    finite = all(m.stats()["nonfinite"] == 0 for m in b.members)
+    if b is not None:
+        e0.record(stream)
+        b.step(K)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(dist, ms)
+    stats = [m.stats() for m in b.members] if b is not None else []
+    diag = reduce_diagnostics(dist, stats)
     # the plain path: every member stepped through its own lbmice_step, one after another
-    L = lbmice.lib()
-    e0.record(stream)
-    for m in b.members:
-        rc = L.lbmice_step(m.handle, K)
-        if rc != lbmice.OK:
-            raise lbmice.LbmiceError(rc, "lbmice_step")
-    e1.record(stream)
-    e1.synchronize()
-    ms_seq = max_over_ranks(dist, e0.elapsed_time(e1))
+    if b is not None:
+        L = lbmice.lib()
+        e0.record(stream)
+        for m in b.members:
+            rc = L.lbmice_step(m.handle, K)
+            if rc != lbmice.OK:
+                raise lbmice.LbmiceError(rc, "lbmice_step")
+        e1.record(stream)
+        e1.synchronize()
+        ms_seq = e0.elapsed_time(e1)
+    ms_seq = max_over_ranks(dist, ms_seq)
     by_side = {}
     for w, s in zip(ws, shapes):
         by_side.setdefault(str(w.nx), "%dx%d" % lbmice.SHAPES[s])
-    out = {"workload": "batch_sweep: %d crystals, sides {256..1024}, PCG64 seed 2101" % len(ws),
-           "members": len(ws), "nodes": int(b.nodes), "steps": K, "ms": ms, "ms_seq": ms_seq,
-           "tile_shape_by_side": by_side, "finite": bool(finite),
-           "gpu_launches_per_step": b.launches_per_step}
-    b.close()
+    out = {"workload": "batch_sweep: %d crystals, sides {256..1024}, PCG64 seed 2101"
+                       % len(ws_all),
+           "members": len(ws_all), "nodes": int(b.nodes) if b is not None else 0,
+           "nodes_all_ranks": int(sum(w.nx * w.ny for w in ws_all)), "steps": K, "ms": ms,
+           "ms_seq": ms_seq, "tile_shape_by_side": by_side,
+           "finite": diag["nonfinite"] == 0, "diagnostics_fp64": diag,
+           "gpu_launches_per_step": launches}
+    if world > 1:
+        out["sharding"] = "by crystal: rank r advances members r, r + %d, ..." % world
+        out["members_per_rank"] = len(ws)
+    if b is not None:
+        b.close()
     return out
 
 
@@ -442,7 +484,7 @@ def run_ours(args):
     # ---- batched sweep: 96 crystals of uneven sizes, one persistent launch per step ----
     batched = None
     if args.batch_steps > 0:
-        batched = run_batched(args, stream, dist)
+        batched = run_batched(args, stream, dist, rank, world)
     gradient = None
     if args.grad_steps > 0:
         gradient = run_gradient(args, stream, dist)
@@ -491,9 +533,10 @@ def run_ours(args):
         "finite": bool(finite and st2["nonfinite"] == 0),
     }
     if batched is not None:
-        batched["value"] = batched["nodes"] * batched["steps"] * world / (
+        # all crystals of all ranks over the slowest rank's time (the sweep is sharded)
+        batched["value"] = batched["nodes_all_ranks"] * batched["steps"] / (
             batched["ms"] * 1e-3) / 1e6
-        batched["plain_sequential_value"] = batched["nodes"] * batched["steps"] * world / (
+        batched["plain_sequential_value"] = batched["nodes_all_ranks"] * batched["steps"] / (
             batched.pop("ms_seq") * 1e-3) / 1e6
         ach = ALGO_BYTES_PER_LUP[("f32", 3)] * batched["nodes"] / (
             batched["ms"] / batched["steps"] * 1e-3) / 1e9
