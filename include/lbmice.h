@@ -51,6 +51,7 @@ extern "C" {
 #define LBMICE_ENONFINITE (-4) /* a NaN or Inf was found in phi, U or rho */
 #define LBMICE_EUNSTABLE (-5)  /* derived relaxation time <= 1/2 or inflow >= sound speed */
 #define LBMICE_ETIMEOUT (-6)   /* a bounded device-side wait gave up */
+#define LBMICE_ENOTSUP (-7)    /* the call needs the checked build (LBMICE_CHECKED)         */
 
 /* ---- boundary kinds of the four faces (Sec. 3.1.3, Sec. 3.2.2) --------------------------
  * PERIODIC: wrap (must be set on both faces of an axis).
@@ -194,6 +195,25 @@ const char* lbmice_strerror(int code);
 /* Name of the CUDA error behind the last LBMICE_ECUDA / LBMICE_ENOMEM returned on the calling
  * thread ("none" if there was none); a static string. */
 const char* lbmice_last_error(void);
+
+/* ---- checked build -------------------------------------------------------------------------
+ * The same sources compiled with -DLBMICE_CHECKED (liblbmice_checked.so; the Python binding
+ * loads it when the environment sets LBMICE_CHECKED=1) test every global and shared-memory
+ * index of the step kernels -- single-grid and batched -- against the extent of its buffer
+ * before the access: population regions (nodes < pstride), [ny][pitch] planes, and the
+ * shared-memory phi and source tiles. A violation sets a bit of a device word (1
+ * population region, 2 plane, 4 shared memory) and the access is skipped, a load giving 0;
+ * nothing traps. It stands in for a memory checker and costs speed; the normal library
+ * compiles the tests away.
+ *
+ * lbmice_debug_flags waits for the device (cudaDeviceSynchronize), writes the word to *flags
+ * and, if clear is 1, resets it. lbmice_debug_set_margin makes the tests use extents shrunk by
+ * margin elements (>= 0; 0 restores them), so that accesses near the end of a buffer, still
+ * inside it, are reported and skipped: a self-test of the checks. Both are process-wide for
+ * the current device. Errors: EINVAL (null flags, clear not 0/1, negative margin), ECUDA; in
+ * the normal library they return LBMICE_ENOTSUP (flags 0). */
+int lbmice_debug_flags(uint32_t* flags, int32_t clear);
+int lbmice_debug_set_margin(int64_t margin);
 
 /* ---- many grids in one launch --------------------------------------------------------------
  * A batch advances many independent grids -- different sizes, supersaturations,

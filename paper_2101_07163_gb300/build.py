@@ -8,6 +8,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "liblbmice.so")
+LIB_CHECKED = os.path.join(HERE, "liblbmice_checked.so")  # -DLBMICE_CHECKED: bounds-checked
 SOURCES = [os.path.join(HERE, "csrc", "lbmice.cu")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "-Xptxas", "-v"]
@@ -23,20 +24,23 @@ def nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile liblbmice.so if it is missing or older than its sources; return its path."""
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in _deps())):
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc()] + NVCC_FLAGS + ["-o", tmp] + SOURCES
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile liblbmice.so (checked: liblbmice_checked.so, every step-kernel index tested
+    against its buffer) if it is missing or older than its sources; return its path."""
+    lib = LIB_CHECKED if checked else LIB
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= max(os.path.getmtime(p) for p in _deps())):
+        return lib
+    tmp = lib + ".tmp%d" % os.getpid()
+    cmd = ([nvcc()] + NVCC_FLAGS + (["-DLBMICE_CHECKED"] if checked else [])
+           + ["-o", tmp] + SOURCES)
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
     if verbose:
         print(res.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -595,8 +595,39 @@ const char* lbmice_strerror(int code) {
     case LBMICE_ENONFINITE: return "non-finite value in phi, U or rho";
     case LBMICE_EUNSTABLE: return "unstable parameters (relaxation time or inflow speed)";
     case LBMICE_ETIMEOUT: return "device-side wait timed out";
+    case LBMICE_ENOTSUP: return "not supported by this build";
     default: return "unknown error";
   }
+}
+
+int lbmice_debug_flags(uint32_t* flags, int32_t clear) {
+  if (!flags || (clear != 0 && clear != 1)) return LBMICE_EINVAL;
+  *flags = 0;
+#ifdef LBMICE_CHECKED
+  LB_TRY(cudaDeviceSynchronize());  // every queued step, on any stream, has run
+  unsigned w = 0;
+  LB_TRY(cudaMemcpyFromSymbol(&w, lbmice::oob_word, sizeof(w)));
+  *flags = w;
+  if (clear) {
+    const unsigned z = 0;
+    LB_TRY(cudaMemcpyToSymbol(lbmice::oob_word, &z, sizeof(z)));
+  }
+  return LBMICE_OK;
+#else
+  return LBMICE_ENOTSUP;
+#endif
+}
+
+int lbmice_debug_set_margin(int64_t margin) {
+  if (margin < 0) return LBMICE_EINVAL;
+#ifdef LBMICE_CHECKED
+  LB_TRY(cudaDeviceSynchronize());
+  const long long m = margin;
+  LB_TRY(cudaMemcpyToSymbol(lbmice::oob_margin, &m, sizeof(m)));
+  return LBMICE_OK;
+#else
+  return LBMICE_ENOTSUP;
+#endif
 }
 
 }  // extern "C"

@@ -22,6 +22,29 @@
 
 namespace lbmice {
 
+// ---- checked build ----------------------------------------------------------------------
+// Compiled with -DLBMICE_CHECKED (liblbmice_checked.so), the step kernels test every global
+// and shared-memory index against the extent of its buffer before the access, in place of a
+// memory checker: a violation sets a bit of the device word oob_word and the access is
+// skipped (a load gives 0), so nothing traps. oob_margin shrinks every extent the tests use
+// by that many elements, so that a test can see the checks fire on accesses that are still
+// inside their buffers. In the normal build every test is the constant true and compiles
+// away.
+enum : unsigned { OOB_POPS = 1u, OOB_PLANE = 2u, OOB_SHARED = 4u };
+#ifdef LBMICE_CHECKED
+__device__ unsigned int oob_word;
+__device__ long long oob_margin;
+__device__ __forceinline__ bool in_range(long long i, long long n, unsigned bit) {
+  if (i >= 0 && i < n - oob_margin) return true;
+  atomicOr(&oob_word, bit);
+  return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_range(long long, long long, unsigned) {
+  return true;
+}
+#endif
+
 // ---- D2Q9 (directions are compile-time after unrolling) ---------------------------------
 __host__ __device__ constexpr int cx_of(int a) {
   return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
@@ -156,6 +179,11 @@ __device__ __forceinline__ long long f32_index(long long pstride, long long node
 // The 9 FP32 populations of one lattice region at a node.
 __device__ __forceinline__ void load_lattice_f32(const float* __restrict__ lat, long long pstride,
                                                  long long node, float* out) {
+  if (!in_range(node, pstride, OOB_POPS)) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) out[a] = 0.0f;
+    return;
+  }
   const float4 p = __ldg(reinterpret_cast<const float4*>(lat + 4 * node));
   const float4 q = __ldg(reinterpret_cast<const float4*>(lat + 4 * pstride + 4 * node));
   out[0] = __ldg(lat + 8 * pstride + node);
@@ -170,6 +198,7 @@ __device__ __forceinline__ void load_lattice_f32(const float* __restrict__ lat, 
 }
 __device__ __forceinline__ void store_lattice_f32(float* __restrict__ lat, long long pstride,
                                                   long long node, const float* v) {
+  if (!in_range(node, pstride, OOB_POPS)) return;
   *reinterpret_cast<float4*>(lat + 4 * node) = make_float4(v[1], v[2], v[3], v[4]);
   *reinterpret_cast<float4*>(lat + 4 * pstride + 4 * node) = make_float4(v[5], v[6], v[7], v[8]);
   lat[8 * pstride + node] = v[0];
@@ -187,6 +216,19 @@ __device__ __forceinline__ void decode9(uint4 v, float M, float* out) {
       M - (((out[1] + out[3]) + (out[2] + out[4])) + ((out[5] + out[7]) + (out[6] + out[8])));
 }
 
+// Checked raw accesses: the 16-byte deviation vector of node `node` of a lattice region (n
+// nodes), and element i of an [ny][pitch] plane of n elements.
+__device__ __forceinline__ uint4 ldg_vec(const uint4* __restrict__ region, long long node,
+                                         long long n) {
+  return in_range(node, n, OOB_POPS) ? __ldg(region + node) : make_uint4(0u, 0u, 0u, 0u);
+}
+__device__ __forceinline__ float ldg_plane(const float* __restrict__ p, long long i, long long n) {
+  return in_range(i, n, OOB_PLANE) ? __ldg(p + i) : 0.0f;
+}
+__device__ __forceinline__ void st_plane(float* __restrict__ p, long long i, long long n, float v) {
+  if (in_range(i, n, OOB_PLANE)) p[i] = v;
+}
+
 // The 9 deviations d_a = p_a - w_a M of one node and lattice from its 16-bit vector v; the
 // rest one is d_0 = -sum_{a>0} d_a, since the populations sum to M.
 template <class S>
@@ -200,6 +242,11 @@ __device__ __forceinline__ void deviations9(uint4 v, float* d) {
 template <class S>
 __device__ __forceinline__ void load9(const typename Storage<S>::T* __restrict__ pops, int L,
                                       long long pstride, long long node, float M, float* out) {
+  if (!in_range(node, pstride, OOB_POPS)) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) out[a] = 0.0f;
+    return;
+  }
   if constexpr (Storage<S>::PLANES) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) out[a] = __ldg(pops + (9 * L + a) * pstride + node);
@@ -215,6 +262,7 @@ template <class S>
 __device__ __forceinline__ void store9(typename Storage<S>::T* __restrict__ pops, int L,
                                        long long pstride, long long node, float M,
                                        const float* p) {
+  if (!in_range(node, pstride, OOB_POPS)) return;
   if constexpr (Storage<S>::PLANES) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) pops[(9 * L + a) * pstride + node] = p[a];

@@ -139,20 +139,21 @@ __device__ __forceinline__ void own_load(const Consts& C, const StepPtrs& P, int
   const long long idx = (long long)Y * C.pitch + X;
   const long long nd = (long long)Y * C.rstride + X;
   const typename ST::T* __restrict__ pops = static_cast<const typename ST::T*>(P.pin);
+  const long long np = (long long)C.pitch * C.ny;
   if constexpr (!ST::DEV) {
     load_lattice_f32(pops + PLANE_H * C.pstride, C.pstride, nd, in.h);
     load_lattice_f32(pops + PLANE_G * C.pstride, C.pstride, nd, in.g);
     if (FLOW) load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, in.f);
   } else {
-    in.h = __ldg(reinterpret_cast<const uint4*>(pops + 8 * nd));
-    in.g = __ldg(reinterpret_cast<const uint4*>(pops + 9 * C.pstride + 8 * nd));
-    in.U = __ldg(P.U_n + idx);
+    in.h = ldg_vec(reinterpret_cast<const uint4*>(pops), nd, C.pstride);
+    in.g = ldg_vec(reinterpret_cast<const uint4*>(pops + 9 * C.pstride), nd, C.pstride);
+    in.U = ldg_plane(P.U_n, idx, np);
     if (FLOW) {
-      in.f = __ldg(reinterpret_cast<const uint4*>(pops + 18 * C.pstride + 8 * nd));
-      in.rho = __ldg(P.rho_n + idx);
+      in.f = ldg_vec(reinterpret_cast<const uint4*>(pops + 18 * C.pstride), nd, C.pstride);
+      in.rho = ldg_plane(P.rho_n, idx, np);
     }
   }
-  in.php = __ldg(P.phi_nm1 + idx);
+  in.php = ldg_plane(P.phi_nm1, idx, np);
 }
 
 // Collide the source node at tile position (sx, sy) in [0, TX+2) x [0, TY+2), global
@@ -167,6 +168,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
                                                const OwnIn<S, FLOW>* pre = nullptr) {
   using T = Tile<TX, TY, R>;
   const int node = sy * T::SW + sx;
+  if (!in_range(node, T::SN, OOB_SHARED)) return;
   int mx = X, my = Y, lx = sx, ly = sy;
   bool mirx = false, miry = false;
   int inlet = -1;
@@ -208,7 +210,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     float rho = 1.0f;
     if (FLOW) {
       if constexpr (ST::DEV) {
-        rho = __ldg(P.rho_n + idx);
+        rho = ldg_plane(P.rho_n, idx, (long long)C.pitch * C.ny);
       } else {
         float fv[9];
         load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, fv);
@@ -231,6 +233,9 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
 
   // ---- populations and moments at time n (Sec. 2.2) ----
   const int pc = (ly + R) * T::PW + (lx + R);
+  if (!in_range(pc - R * (T::PW + 1), T::PN, OOB_SHARED) ||
+      !in_range(pc + R * (T::PW + 1), T::PN, OOB_SHARED))
+    return;
   const float ph = sphi[pc];
   // FP32: the populations. 16-bit: their deviations d_a = p_a - w_a M from the stored
   // moments M (phi, U, rho), with d_0 = -sum_{a>0} d_a; the moments are the stored ones and
@@ -262,15 +267,16 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
       if (FLOW) load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, fv);
     } else {
       const uint4* pv = reinterpret_cast<const uint4*>(pops);
-      deviations9<S>(__ldg(pv + nd), hv);
-      deviations9<S>(__ldg(pv + (9 * C.pstride) / 8 + nd), gv);
-      U = __ldg(P.U_n + idx);
+      const long long np = (long long)C.pitch * C.ny;
+      deviations9<S>(ldg_vec(pv, nd, C.pstride), hv);
+      deviations9<S>(ldg_vec(pv + (9 * C.pstride) / 8, nd, C.pstride), gv);
+      U = ldg_plane(P.U_n, idx, np);
       if (FLOW) {
-        deviations9<S>(__ldg(pv + (18 * C.pstride) / 8 + nd), fv);
-        rho = __ldg(P.rho_n + idx);
+        deviations9<S>(ldg_vec(pv + (18 * C.pstride) / 8, nd, C.pstride), fv);
+        rho = ldg_plane(P.rho_n, idx, np);
       }
     }
-    php = __ldg(P.phi_nm1 + idx);
+    php = ldg_plane(P.phi_nm1, idx, (long long)C.pitch * C.ny);
   }
   if constexpr (!ST::DEV) {
     U = sum9(gv);
@@ -425,7 +431,9 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
     const int pitch = (int)C.pitch;
     for (int i = tid; i < T::PN; i += T::NT) {
       const int lx = i % T::PW, ly = i / T::PW;
-      sphi[i] = __ldg(pb + ly * pitch + lx);
+      if (in_range((long long)(y0 - H + ly) * C.pitch + (x0 - H + lx),
+                   (long long)C.pitch * C.ny, OOB_PLANE))
+        sphi[i] = __ldg(pb + ly * pitch + lx);
     }
   } else
   for (int i = tid; i < T::PN; i += T::NT) {
@@ -437,7 +445,7 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
       v = 0.0f;  // beyond the grid's halo (ragged last tile): never read
     } else if (axis_phi(X, C.nx, C.bc[0], C.bc[1], gx) &&
                axis_phi(Y, C.ny, C.bc[2], C.bc[3], gy)) {
-      v = __ldg(P.phi_n + (long long)gy * C.pitch + gx);
+      v = ldg_plane(P.phi_n, (long long)gy * C.pitch + gx, (long long)C.pitch * C.ny);
     }
     sphi[i] = v;
   }
@@ -467,6 +475,11 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
   const int X = x0 + tx, Y = y0 + ty;
   if (X >= C.nx || Y >= C.ny) return;  // (this thread has no node in this tile)
   const long long idx = (long long)Y * C.pitch + X;
+  const long long np = (long long)C.pitch * C.ny;
+  // the nine pull sources span tile positions ty..ty+2 x tx..tx+2
+  if (!in_range(ty * T::SW + tx, T::SN, OOB_SHARED) ||
+      !in_range((ty + 2) * T::SW + tx + 2, T::SN, OOB_SHARED))
+    return;
   float hn[9];
   if constexpr (!ST::DEV) {
     // FP32 storage: each lattice's pulled populations go back as two float4 and a float
@@ -483,7 +496,7 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
     store_lattice_f32(po + PLANE_H * C.pstride, C.pstride, nd, hn);
     store_lattice_f32(po + PLANE_G * C.pstride, C.pstride, nd, gn);
     if (FLOW) store_lattice_f32(po + PLANE_F * C.pstride, C.pstride, nd, fn);
-    P.phi_np1[idx] = sum9(hn);
+    st_plane(P.phi_np1, idx, np, sum9(hn));
   } else {
     // 16-bit storage: the moments of the pulled populations are stored in FP32 and the
     // moving populations as deviations from them
@@ -496,16 +509,16 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
       if (FLOW) fn[a] = spost[(PLANE_F + a) * T::SN + src];
     }
     const float phin = sum9(hn);
-    P.phi_np1[idx] = phin;
+    st_plane(P.phi_np1, idx, np, phin);
     typename ST::T* __restrict__ pout = static_cast<typename ST::T*>(P.pout);
     const long long nd = (long long)Y * C.rstride + X;
     store9<S>(pout, 0, C.pstride, nd, phin, hn);
     const float Un = sum9(gn);
-    P.U_np1[idx] = Un;
+    st_plane(P.U_np1, idx, np, Un);
     store9<S>(pout, 1, C.pstride, nd, Un, gn);
     if (FLOW) {
       const float rn = sum9(fn);
-      P.rho_np1[idx] = rn;
+      st_plane(P.rho_np1, idx, np, rn);
       store9<S>(pout, 2, C.pstride, nd, rn, fn);
     }
   }

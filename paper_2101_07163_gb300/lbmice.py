@@ -12,9 +12,11 @@ import os
 
 import numpy as np
 
-from .build import LIB
+from .build import LIB, LIB_CHECKED
 
-OK, EINVAL, ECUDA, ENOMEM, ENONFINITE, EUNSTABLE, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ECUDA, ENOMEM, ENONFINITE, EUNSTABLE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+# bits of the checked build's violation word (lbmice_debug_flags)
+OOB_POPS, OOB_PLANE, OOB_SHARED = 1, 2, 4
 BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FREESLIP = 0, 1, 2, 3
 PHI, U, RHO, UX, UY, PHI_PREV, POPS, STATE = 0, 1, 2, 3, 4, 5, 6, 7
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
@@ -28,7 +30,8 @@ EXPORTS = ("lbmice_params_default", "lbmice_create", "lbmice_init_seed", "lbmice
            "lbmice_batch_member", "lbmice_batch_step", "lbmice_batch_autotune",
            "lbmice_batch_set_shape", "lbmice_batch_destroy", "lbmice_last_error",
            "lbmice_tape_create", "lbmice_tape_record", "lbmice_tape_steps",
-           "lbmice_tape_backward", "lbmice_tape_destroy")
+           "lbmice_tape_backward", "lbmice_tape_destroy", "lbmice_debug_flags",
+           "lbmice_debug_set_margin")
 
 
 class LbmiceError(RuntimeError):
@@ -62,13 +65,20 @@ class Params(ctypes.Structure):
 _lib = None
 
 
+def lib_path() -> str:
+    """liblbmice.so, or the bounds-checked liblbmice_checked.so when the environment sets
+    LBMICE_CHECKED=1."""
+    return LIB_CHECKED if os.environ.get("LBMICE_CHECKED") == "1" else LIB
+
+
 def lib():
     """Load liblbmice.so (built by __graft_entry__.build()); raise if it is missing."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
-            raise RuntimeError(f"{LIB} is not built; run __graft_entry__.build() first")
-        L = ctypes.CDLL(LIB)
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built; run __graft_entry__.build() first")
+        L = ctypes.CDLL(path)
         vp, dp, i32, i64, sz = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                 ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t)
         pp = ctypes.POINTER(Params)
@@ -97,6 +107,8 @@ def lib():
         L.lbmice_tape_steps.restype = i64
         L.lbmice_tape_backward.argtypes = [vp, vp, vp, dp, vp, vp, vp, vp, vp]
         L.lbmice_tape_destroy.argtypes = [vp]
+        L.lbmice_debug_flags.argtypes = [ctypes.POINTER(ctypes.c_uint32), i32]
+        L.lbmice_debug_set_margin.argtypes = [i64]
         _lib = L
     return _lib
 
@@ -446,3 +458,16 @@ class Tape:
             self.close()
         except Exception:
             pass
+
+
+def debug_flags(clear: bool = True) -> int:
+    """The checked build's violation word (OOB_* bits), reset if clear; raises LbmiceError
+    (ENOTSUP) with the normal library."""
+    w = ctypes.c_uint32()
+    _check(lib().lbmice_debug_flags(ctypes.byref(w), int(bool(clear))), "lbmice_debug_flags")
+    return int(w.value)
+
+
+def debug_set_margin(margin: int):
+    """Checked build: shrink every extent its index tests use by margin elements."""
+    _check(lib().lbmice_debug_set_margin(int(margin)), "lbmice_debug_set_margin")

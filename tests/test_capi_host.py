@@ -114,3 +114,15 @@ def test_lattice_refuses_to_run_without_cuda():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         lbmice.Lattice(16, 16)
+
+
+def test_normal_library_reports_that_it_has_no_checks():
+    # the bounds-checked entry points exist in every build; without -DLBMICE_CHECKED they
+    # touch no device and answer ENOTSUP
+    L = lbmice.lib()
+    w = ctypes.c_uint32(7)
+    assert L.lbmice_debug_flags(ctypes.byref(w), 1) == lbmice.ENOTSUP and w.value == 0
+    assert L.lbmice_debug_flags(None, 0) == lbmice.EINVAL
+    assert L.lbmice_debug_flags(ctypes.byref(w), 2) == lbmice.EINVAL
+    assert L.lbmice_debug_set_margin(0) == lbmice.ENOTSUP
+    assert L.lbmice_debug_set_margin(-1) == lbmice.EINVAL
