@@ -3,6 +3,7 @@ the four-fold anisotropy of the validation system of Sec. 3.1.2): exactness and 
 of every stencil, the four-fold a_s and flux against their trigonometric form, and bit-exact
 mirror symmetry with every stencil."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -107,3 +108,62 @@ def test_stencils_and_folds_are_validated():
     with pytest.raises(ValueError):
         Oracle(nx=8, ny=8, fold=5)
     Oracle(nx=8, ny=8, stencil=8, fold=4)  # accepted
+
+
+# ---- the printed tables -------------------------------------------------------------------
+
+SHELLS = {1: [(1, 0)], 2: [(1, 1)], 4: [(2, 0)], 5: [(1, 2), (2, 1)], 8: [(2, 2)]}
+
+
+@pytest.mark.parametrize("stencil", [4, 6, 8])
+def test_stencil_weights_are_those_of_table_1(stencil):
+    # A field that is 1 at one neighbour x0 + c and 0 elsewhere: the oracle's gradient at x0
+    # is w(|c|^2) c with the weight printed in Table 1 (tests/golden), for every neighbour of
+    # every shell of the stencil in all four quadrants -- and 0 for shells the stencil lacks.
+    from tests.helpers import golden_constants
+    g = golden_constants("table1_isotropic_weights.txt")
+    n, x0, y0 = 12, 6, 6
+    for shell, reps in SHELLS.items():
+        w = g.get(f"E{stencil}_w{shell}", 0.0)
+        for (ax, ay) in reps:
+            for sx in (1, -1):
+                for sy in (1, -1):
+                    cx, cy = sx * ax, sy * ay
+                    phi = np.zeros((n, n))
+                    phi[y0 + cy, x0 + cx] = 1.0
+                    gx, gy = oracle.gradient_stencil(phi, stencil)
+                    assert gx[y0, x0] == pytest.approx(w * cx, abs=1e-15), (shell, cx, cy)
+                    assert gy[y0, x0] == pytest.approx(w * cy, abs=1e-15), (shell, cx, cy)
+
+
+def table2_rows():
+    from tests.helpers import GOLDEN
+    consts, rows = {}, []
+    with open(os.path.join(GOLDEN, "table2_plate_regime.txt")) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            if "=" in line:
+                k, v = (t.strip() for t in line.split("=", 1))
+                consts[k] = float(v)
+            else:
+                nr, name, U0, L_sat, rho0, drho = line.split()
+                rows.append((int(nr), name, float(U0), float(L_sat), float(rho0), float(drho)))
+    return consts, rows
+
+
+def test_table2_workloads_follow_the_printed_table():
+    # The workloads of the seven morphologies carry Table 2's U0 and L_sat; the table's own
+    # densities give its U0 through U = (drho + rho_sat_W - rho_sat_I) / rho_sat_I and
+    # rho0 = rho_sat_W + drho (to the rounding of the printed digits), which is why U0 and
+    # L_sat are the only inputs (reading of Sec. 3.2.1).
+    from paper_2101_07163_gb300 import workloads as W
+    c, rows = table2_rows()
+    assert len(rows) == len(W.TABLE2_WORKLOADS) == 7
+    for (nr, name, U0, L_sat, rho0, drho), w in zip(rows, W.TABLE2_WORKLOADS):
+        assert w.name.startswith(f"table2_{nr}_{name}_")
+        assert w.U0 == U0 and w.L_sat == L_sat
+        assert (drho + c["rho_sat_W"] - c["rho_sat_I"]) / c["rho_sat_I"] == pytest.approx(U0, abs=1e-3)
+        assert rho0 - drho == pytest.approx(c["rho_sat_W"], abs=1e-3)
+        assert (w.dx, w.dt, w.lam, w.eps, w.nx, w.ny) == (0.8, 0.05, 3.0, 0.05, 400, 400)
