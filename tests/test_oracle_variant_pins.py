@@ -167,3 +167,27 @@ def test_table2_workloads_follow_the_printed_table():
         assert (drho + c["rho_sat_W"] - c["rho_sat_I"]) / c["rho_sat_I"] == pytest.approx(U0, abs=1e-3)
         assert rho0 - drho == pytest.approx(c["rho_sat_W"], abs=1e-3)
         assert (w.dx, w.dt, w.lam, w.eps, w.nx, w.ny) == (0.8, 0.05, 3.0, 0.05, 400, 400)
+
+
+def test_validation_workloads_convert_the_printed_parameters():
+    # The isotropy system of Sec. 3.1.1 is printed in physical units; in W0 / tau0 units it is
+    # dx = 0.8, dt = 0.096 and D = kappa tau0 / W0^2 = 1. The four-fold system of Sec. 3.1.2 is
+    # printed in those units already; its lambda is the beta = 0 value of D = kappa = 4.
+    from tests.helpers import golden_constants
+    from paper_2101_07163_gb300 import workloads as W
+    g = golden_constants("validation_systems.txt")
+    for s, w in W.ISOTROPY.items():
+        assert w.stencil == s
+        assert w.dx == pytest.approx(g["iso_dx"] / g["iso_W0"], rel=1e-12)
+        assert w.dt == pytest.approx(g["iso_dt"] / g["iso_tau0"], rel=1e-12)
+        assert w.D == pytest.approx(g["iso_kappa"] * g["iso_tau0"] / g["iso_W0"] ** 2, rel=1e-12)
+        assert (w.U0, w.lam, w.eps) == (g["iso_undercooling"], g["iso_lambda"], g["iso_eps"])
+        assert (w.nx, w.ny, w.R0, w.steps) == (g["iso_n"], g["iso_n"], g["iso_seed_radius_cells"],
+                                               g["iso_steps"])
+    for w, U0, n in ((W.FOURFOLD_030, g["ff_U0_a"], g["ff_n_a"]),
+                     (W.FOURFOLD_055, g["ff_U0_b"], g["ff_n_b"])):
+        assert (w.dx, w.dt, w.D, w.eps, w.fold) == (g["ff_dx"], g["ff_dt"], g["ff_kappa"],
+                                                    g["ff_eps"], 4)
+        assert (w.U0, w.nx, w.ny, w.R0) == (U0, n, n, g["ff_seed_radius_cells"])
+        o = Oracle(nx=8, ny=8, **w.params())
+        assert o.derived()["lambda"] == pytest.approx(g["ff_lambda"], abs=1e-4)
