@@ -91,7 +91,8 @@ extern "C" {
 
 /* ---- parameters (Sec. 2.1, Sec. 2.2, Sec. 3) -------------------------------------------- */
 typedef struct lbmice_params {
-  int32_t nx, ny;       /* grid nodes, each >= 4                                           */
+  int32_t nx, ny;       /* grid nodes, each >= 4, with pitch * ny < 2^31 (pitch = nx rounded
+                           up to 32); larger offsets are 64-bit throughout                 */
   double dx, dt;        /* grid and time step (default 0.4, 0.008)                         */
   double W0, tau0;      /* interface width and time (default 1, 1)                         */
   double D;             /* vapour diffusivity (default 2)                                  */

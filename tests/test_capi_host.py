@@ -71,6 +71,7 @@ def test_params_default_and_strerror(L):
     (dict(storage=3), lbmice.EINVAL),
     (dict(stencil=3), lbmice.EINVAL),
     (dict(fold=5), lbmice.EINVAL),
+    (dict(nx=46368, ny=46320), lbmice.EINVAL),  # pitch * ny = 2^31 + 282112 nodes: too many
 ])
 def test_create_rejects_bad_parameters_without_a_gpu(L, change, code):
     kw = dict(nx=16, ny=16)
