@@ -14,6 +14,9 @@
  *     time factor, source Q = phi - phi^3 + lambda U (1 - phi^2)^2, and anisotropy
  *     a_s = 1 + eps cos(6 theta) from the E4 isotropic gradient of phi (Sec. 3.1.1,
  *     Table 1).
+ * Options (lbmice_params): the gradient stencil E2, E4, E6 or E8 (Sec. 3.1.1), the four-fold
+ * anisotropy of the validation system (Sec. 3.1.2), and FP16 or BF16 storage of the
+ * populations as deviations from their FP32 moments (arithmetic stays FP32).
  * Unit conventions: W0, tau0, dx, dt and D share one unit system (the paper's validation
  * units are W0 = tau0 = 1, dx = 0.4, dt = 0.008, Sec. 3.1.2); u_in and nu are in lattice
  * units (dx/dt, dx^2/dt).
