@@ -240,6 +240,8 @@ class Lattice:
         if out is not None:
             if out.numel() * 4 < self.nx * self.ny or out.dtype.itemsize != 4:
                 raise ValueError("out must be a float32 tensor of nx*ny elements")
+            if not out.is_cuda or out.device != self.device or not out.is_contiguous():
+                raise ValueError("out must be a contiguous CUDA tensor on the lattice's device")
             _check(lib().lbmice_fields(self._h, int(which), ctypes.c_void_p(out.data_ptr()),
                                        out.numel() * 4, 1), "lbmice_fields")
             return out

@@ -342,6 +342,24 @@ def test_device_fields_equal_host_fields():
     np.testing.assert_array_equal(out.cpu().numpy(), a.field(lbmice.PHI))
 
 
+def test_field_output_tensor_is_checked():
+    # a device output must be a contiguous float32 CUDA tensor on the lattice's device
+    import torch
+    w = channel_workload("o", 32, 16, (W.BC_PERIODIC,) * 4)
+    lat = lbmice.Lattice(w.nx, w.ny, **w.params())
+    lat.init_seed(w.cx, w.cy, w.R0, w.U0)
+    good = torch.empty((w.ny, w.nx), dtype=torch.float32, device=lat.device)
+    assert lat.field(lbmice.PHI, out=good) is good
+    np.testing.assert_array_equal(good.cpu().numpy(), lat.field(lbmice.PHI))
+    bad = (torch.empty((w.ny, w.nx), dtype=torch.float32),                            # host
+           torch.empty((w.ny, 2 * w.nx), dtype=torch.float32, device=lat.device)[:, ::2],
+           torch.empty((w.ny, w.nx), dtype=torch.float64, device=lat.device))
+    for t in bad:
+        with pytest.raises(ValueError):
+            lat.field(lbmice.PHI, out=t)
+    lat.close()
+
+
 def test_bad_buffer_sizes_are_rejected():
     w = channel_workload("b", 32, 16, (W.BC_PERIODIC,) * 4)
     lat = lbmice.Lattice(w.nx, w.ny, **w.params())
