@@ -56,6 +56,24 @@ class Workload:
                     U_in=self.U_in, u_in=self.u_in, nu=self.nu, bc=tuple(self.bc),
                     flow=self.flow, stencil=self.stencil, fold=self.fold)
 
+    def to_dict(self) -> dict:
+        """Every field, JSON-serialisable (the face kinds as a list)."""
+        d = dataclasses.asdict(self)
+        d["bc"] = list(self.bc)
+        return d
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Workload":
+        """The inverse of to_dict; unknown keys are refused."""
+        names = {f.name for f in dataclasses.fields(cls)}
+        extra = set(d) - names
+        if extra:
+            raise ValueError(f"unknown workload keys: {sorted(extra)}")
+        kw = dict(d)
+        if "bc" in kw:
+            kw["bc"] = tuple(int(b) for b in kw["bc"])
+        return cls(**kw)
+
     def with_size(self, nx: int, ny: int, **kw) -> "Workload":
         """The same physics on another grid, the seed kept at the same relative place."""
         return dataclasses.replace(self, nx=nx, ny=ny, cx=self.cx * nx / self.nx,
@@ -196,3 +214,18 @@ def batch_sweep(count: int = 96, seed: int = 2101, sides=C4_SIDES, steps: int = 
                             u_in=u, nu=0.016, bc=tuple(bc), flow=True, cx=n / 2, cy=n / 2,
                             R0=6.0))
     return out
+
+
+def named() -> dict:
+    """Every named workload as {name: to_dict()}: the single-grid configurations (the 128^2
+    seed, the ventilated channel, the 2048^2 plate) and the paper's Table 2, four-fold and
+    isotropy systems. The batched sweep's members come from batch_sweep()."""
+    return {name: w.to_dict() for name, w in sorted(WORKLOADS.items())}
+
+
+if __name__ == "__main__":
+    # python -m paper_2101_07163_gb300.workloads [name ...]: the named workloads as JSON
+    import json
+    import sys
+    want = sys.argv[1:] or sorted(WORKLOADS)
+    print(json.dumps({n: WORKLOADS[n].to_dict() for n in want}, indent=1))
