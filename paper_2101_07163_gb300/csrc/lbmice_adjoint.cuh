@@ -12,7 +12,8 @@
 //     downstream nodes x + c_a, recomputes the collision of x and runs it backwards: writes the
 //     collision part of the population adjoints, the node-local part of the phi^n adjoint,
 //     the adjoint of the node's E4 gradient, the adjoint of phi^{n-1}, B = 1 - 1/a_s^2, and
-//     accumulates the parameter adjoints (FP64, one slot per block: deterministic).
+//     accumulates the parameter adjoints (FP32 within a warp, FP64 across warps, blocks
+//     and steps; one slot per block: deterministic).
 //   adj_pull_kernel (per node y): adds the pull's own-population term
 //     h_a^{n+1}(y) = h_a^n(y) B(y - c_a) + ..., and gathers the transpose of the E4 stencil.
 // Non-differentiable points are taken as the branch the forward step takes: below the
