@@ -314,7 +314,7 @@ def run_batched(args, stream, dist, rank: int = 0, world: int = 1):
     ms_seq = max_over_ranks(dist, ms_seq)
     by_side = {}
     for w, s in zip(ws, shapes):
-        by_side.setdefault(str(w.nx), "%dx%d" % lbmice.SHAPES[s])
+        by_side.setdefault(str(w.nx), lbmice.SHAPES[s])
     out = {"workload": "batch_sweep: %d crystals, sides {256..1024}, PCG64 seed 2101"
                        % len(ws_all),
            "members": len(ws_all), "nodes": int(b.nodes) if b is not None else 0,

@@ -221,26 +221,33 @@ int lbmice_debug_set_margin(int64_t margin);
 
 /* ---- many grids in one launch --------------------------------------------------------------
  * A batch advances many independent grids -- different sizes, supersaturations,
- * anisotropies, inflows and faces -- with one kernel launch per time step for every tile
- * shape in use (and per LBMICE_BATCH_MAX_PER_LAUNCH members of that shape), captured in CUDA
- * graphs of 60 steps, instead of one launch per grid. Each launch carries its members'
- * constants and buffer roles in its kernel parameters (no device-side list), one CTA per tile
- * of the concatenated member tilings. Its members are ordinary handles: initialise, read and
- * check them with the single-grid calls through lbmice_batch_member. All members share the
- * flow flag and the storage, and advance in lockstep: lbmice_batch_step refuses (EINVAL) once
- * a member was stepped on its own (re-initialising every member restarts them together).
- * There is no device-side wait in the batched path.                                        */
+ * anisotropies, inflows and faces -- with one kernel launch per time step for every shape
+ * in use (and per LBMICE_BATCH_MAX_PER_LAUNCH members of that shape), captured in CUDA graphs
+ * of 60 steps, instead of one launch per grid. Each launch carries its members' constants
+ * and buffer roles in its kernel parameters (no device-side list). The march shape is one
+ * wave of persistent CTAs over the concatenated column strips of its members (each CTA an
+ * equal share of their rows); a tile shape is one CTA per tile of the concatenated member
+ * tilings. Every shape collides a node with the same arithmetic, so a member's results do
+ * not depend on its shape, and equal those of lbmice_step bit for bit. Members are ordinary
+ * handles: initialise, read and check them with the single-grid calls through
+ * lbmice_batch_member. All members share the flow flag and the storage, and advance in
+ * lockstep: lbmice_batch_step refuses (EINVAL) once a member was stepped on its own
+ * (re-initialising every member restarts them together). There is no device-side wait in
+ * the batched path.                                                                         */
 typedef struct lbmice_batch lbmice_batch_t;
 
-/* Tile shapes of 256 threads the batched kernel can use (autotuned per grid size). */
-#define LBMICE_SHAPE_32x8 0
-#define LBMICE_SHAPE_64x4 1
-#define LBMICE_SHAPE_16x16 2
+/* Shapes the batched step can use for a member (autotuned per grid size): the column march
+ * of the single-grid step, or a 2D tile of 256 threads that collides its tile plus a
+ * one-node ring. */
+#define LBMICE_SHAPE_MARCH 0
+#define LBMICE_SHAPE_32x8 1
+#define LBMICE_SHAPE_64x4 2
+#define LBMICE_SHAPE_16x16 3
 /* Members one batched launch can carry (its parameter block stays under 32 KB). */
 #define LBMICE_BATCH_MAX_PER_LAUNCH 128
 
 /* Create count member grids from params[0..count-1] on stream (as lbmice_create each), all
- * with tile shape 32x8. The batched tile is the default scheme only: every member takes the
+ * with the march shape. The batched step is the default scheme only: every member takes the
  * E4 gradient and the six-fold anisotropy (stencil 0 or 4, fold 0 or 6). Errors: EINVAL
  * (count < 1, null, mixed flow or storage, another stencil or fold, any member's
  * parameters), EUNSTABLE, ENOMEM, ECUDA; nothing is leaked on error. */
@@ -252,13 +259,13 @@ int lbmice_batch_create(const lbmice_params* params, int32_t count, void* stream
 int32_t lbmice_batch_size(const lbmice_batch_t* b);
 lbmice_t* lbmice_batch_member(lbmice_batch_t* b, int32_t i);
 
-/* Advance every member by nsteps: per step, one launch per tile shape in use and per
+/* Advance every member by nsteps: per step, one launch per shape in use and per
  * LBMICE_BATCH_MAX_PER_LAUNCH members of that shape. Errors: EINVAL (members out of
  * lockstep), ECUDA. Asynchronous. */
 int lbmice_batch_step(lbmice_batch_t* b, int64_t nsteps);
 
 /* Autotuner: for each distinct grid size, time steps_per_trial steps of those members with
- * each tile shape (CUDA events) and keep the fastest. Every member is advanced by the same
+ * each shape (CUDA events) and keep the fastest. Every member is advanced by the same
  * number of steps (written to *steps_taken), so the batch stays in lockstep; initialise the
  * members again afterwards if the run must start from its initial state. shapes (optional,
  * host, count entries) receives the chosen shape of each member. Synchronises the stream.
@@ -266,7 +273,7 @@ int lbmice_batch_step(lbmice_batch_t* b, int64_t nsteps);
 int lbmice_batch_autotune(lbmice_batch_t* b, int32_t steps_per_trial, int32_t* shapes,
                           int64_t* steps_taken);
 
-/* Set the tile shape of member i (LBMICE_SHAPE_*); launches already queued keep the shapes
+/* Set the shape of member i (LBMICE_SHAPE_*); launches already queued keep the shapes
  * they were given. Errors: EINVAL. */
 int lbmice_batch_set_shape(lbmice_batch_t* b, int32_t i, int32_t shape);
 

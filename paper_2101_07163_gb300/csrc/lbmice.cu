@@ -166,26 +166,43 @@ int with_storage(const lbmice_t* h, Fn&& fn) {
   }
 }
 
+// Launch grid of the march over one grid: one CTA per (strip, segment of rows).
+dim3 march_grid(const Consts& C) {
+  const int H = march_seg_rows(C.ny);
+  return dim3(march_strips(C.nx), (C.ny + H - 1) / H);
+}
+long long march_units(const Consts& C) {
+  const int H = march_seg_rows(C.ny);
+  return (long long)march_strips(C.nx) * ((C.ny + H - 1) / H);
+}
+
 // One step of grid h on the given buffers.
 int launch_step_ptrs(const lbmice_t* h, const StepPtrs& P, cudaStream_t st) {
-  const dim3 grd((h->C.nx + kTX - 1) / kTX, (h->C.ny + kTY - 1) / kTY), blk(kTX * kTY);
-  auto launch = [&](auto radius) {
-    constexpr int R = decltype(radius)::value;
+  if (h->C.stencil == 4 && h->C.fold == 6) {
+    // the default scheme (E4, six-fold): the column march
+    const dim3 grid = march_grid(h->C);
     return with_storage(h, [&](auto tag) {
       using S = decltype(tag);
       if (h->p.flow)
-        step_kernel<kTX, kTY, true, S, R>
-            <<<grd, blk, Tile<kTX, kTY, R>::template smem_bytes<true>(), st>>>(h->C, P);
+        march_kernel<true, S><<<grid, kMarchThreads, march_smem_bytes<true>(), st>>>(h->C, P);
       else
-        step_kernel<kTX, kTY, false, S, R>
-            <<<grd, blk, Tile<kTX, kTY, R>::template smem_bytes<false>(), st>>>(h->C, P);
+        march_kernel<false, S><<<grid, kMarchThreads, march_smem_bytes<false>(), st>>>(h->C, P);
       return cuda_err(cudaGetLastError());
     });
-  };
-  // The default (E4, six-fold) runs on the specialised radius-1 tile; every other stencil
-  // and fold on the general tile of radius 2 (E6 and E8 reach two nodes out: phi halo 3)
-  return h->C.stencil == 4 && h->C.fold == 6 ? launch(std::integral_constant<int, 1>{})
-                                             : launch(std::integral_constant<int, 2>{});
+  }
+  // every other stencil and fold: the 2D tile of radius 2 (E6 and E8 reach two nodes out:
+  // phi halo 3)
+  const dim3 grd((h->C.nx + kTX - 1) / kTX, (h->C.ny + kTY - 1) / kTY), blk(kTX * kTY);
+  return with_storage(h, [&](auto tag) {
+    using S = decltype(tag);
+    if (h->p.flow)
+      step_kernel<kTX, kTY, true, S, 2>
+          <<<grd, blk, Tile<kTX, kTY, 2>::template smem_bytes<true>(), st>>>(h->C, P);
+    else
+      step_kernel<kTX, kTY, false, S, 2>
+          <<<grd, blk, Tile<kTX, kTY, 2>::template smem_bytes<false>(), st>>>(h->C, P);
+    return cuda_err(cudaGetLastError());
+  });
 }
 
 // Step s of grid h on its own rotating buffers.
@@ -724,9 +741,11 @@ namespace {
 // count (which re-initialising every member resets) decides the buffer phase.
 int64_t batch_steps(const lbmice_batch_t* b) { return b->members[0]->step; }
 
-int member_tiles(const lbmice_t* m, int shape) {
+// Work units of a member in a launch of this shape: tiles, or (strip, row) pairs of the march.
+long long member_units(const lbmice_t* m, int shape) {
+  if (shape == LBMICE_SHAPE_MARCH) return march_units(m->C);
   const int tx = shape_tx(shape), ty = shape_ty(shape);
-  return ((m->C.nx + tx - 1) / tx) * ((m->C.ny + ty - 1) / ty);
+  return (long long)((m->C.nx + tx - 1) / tx) * ((m->C.ny + ty - 1) / ty);
 }
 
 // Buffer roles of step phase ph (step mod 6), as the single-grid path rotates them.
@@ -745,20 +764,33 @@ StepPtrs step_ptrs(const lbmice_t* h, int ph) {
 }
 
 template <int TX, int TY>
-int launch_block(const lbmice_batch_t* b, int tiles, cudaStream_t st) {
+int launch_block(const lbmice_batch_t* b, long long tiles, cudaStream_t st) {
   return with_storage(b->members[0], [&](auto tag) {
     using S = decltype(tag);
     if (b->flow)
       batch_step_kernel<TX, TY, true, S>
-          <<<tiles, TX * TY, Tile<TX, TY>::template smem_bytes<true>(), st>>>(*b->block);
+          <<<(unsigned)tiles, TX * TY, Tile<TX, TY>::template smem_bytes<true>(), st>>>(*b->block);
     else
       batch_step_kernel<TX, TY, false, S>
-          <<<tiles, TX * TY, Tile<TX, TY>::template smem_bytes<false>(), st>>>(*b->block);
+          <<<(unsigned)tiles, TX * TY, Tile<TX, TY>::template smem_bytes<false>(), st>>>(*b->block);
     return cuda_err(cudaGetLastError());
   });
 }
 
-// One step (phase ph) of the listed members: one launch per tile shape in use and per
+int launch_march_block(const lbmice_batch_t* b, long long units, cudaStream_t st) {
+  return with_storage(b->members[0], [&](auto tag) {
+    using S = decltype(tag);
+    if (b->flow)
+      batch_march_kernel<true, S>
+          <<<(unsigned)units, kMarchThreads, march_smem_bytes<true>(), st>>>(*b->block);
+    else
+      batch_march_kernel<false, S>
+          <<<(unsigned)units, kMarchThreads, march_smem_bytes<false>(), st>>>(*b->block);
+    return cuda_err(cudaGetLastError());
+  });
+}
+
+// One step (phase ph) of the listed members: one launch per shape in use and per
 // kBatchMaxMembers members of that shape.
 int launch_members(lbmice_batch_t* b, const std::vector<int>& idx, int ph, cudaStream_t st) {
   for (int s = 0; s < kNumShapes; ++s) {
@@ -774,16 +806,18 @@ int launch_members(lbmice_batch_t* b, const std::vector<int>& idx, int ph, cudaS
         BatchDesc& d = L.d[L.n];
         d.C = h->C;
         d.P = step_ptrs(h, ph);
-        d.tiles_x = (h->C.nx + shape_tx(s) - 1) / shape_tx(s);
+        d.tiles_x = s == LBMICE_SHAPE_MARCH ? march_strips(h->C.nx)
+                                            : (h->C.nx + shape_tx(s) - 1) / shape_tx(s);
         d.pad_ = 0;
-        L.tile_start[L.n + 1] = L.tile_start[L.n] + member_tiles(h, s);
+        L.tile_start[L.n + 1] = L.tile_start[L.n] + member_units(h, s);
         ++L.n;
       }
       if (L.n == 0) break;
-      const int tiles = L.tile_start[L.n];
-      const int rc = s == LBMICE_SHAPE_32x8   ? launch_block<32, 8>(b, tiles, st)
-                     : s == LBMICE_SHAPE_64x4 ? launch_block<64, 4>(b, tiles, st)
-                                              : launch_block<16, 16>(b, tiles, st);
+      const long long units = L.tile_start[L.n];
+      const int rc = s == LBMICE_SHAPE_MARCH  ? launch_march_block(b, units, st)
+                     : s == LBMICE_SHAPE_32x8 ? launch_block<32, 8>(b, units, st)
+                     : s == LBMICE_SHAPE_64x4 ? launch_block<64, 4>(b, units, st)
+                                              : launch_block<16, 16>(b, units, st);
       if (rc != LBMICE_OK) return rc;
       if (k >= idx.size()) break;
     }
@@ -851,7 +885,7 @@ int lbmice_batch_create(const lbmice_params* params, int32_t count, void* stream
   b->flow = params[0].flow;
   b->storage = params[0].storage;
   b->members.assign(count, nullptr);
-  b->shape.assign(count, LBMICE_SHAPE_32x8);
+  b->shape.assign(count, LBMICE_SHAPE_MARCH);
   for (int i = 0; i < count; ++i) {
     const int rc = lbmice_create(&params[i], stream, &b->members[i]);
     if (rc != LBMICE_OK) {

@@ -26,7 +26,7 @@
 namespace lbmice {
 
 // Buffers of one reverse step. The forward populations are in the step's node-interleaved
-// FP32 layout (load_lattice_f32, f32_index); their adjoints are plain planes,
+// FP32 layout (load_hg_f32, load_lattice_f32, f32_pop_index); their adjoints are plain planes,
 // q * pstride + y * rstride + x; every other plane is [ny][pitch].
 struct AdjPtrs {
   const float* pops;     // forward state n: populations
@@ -96,10 +96,17 @@ __global__ void __launch_bounds__(256, 3) adj_collide_kernel(const Consts C, con
     // ---- forward recomputation of the node's collision (the step kernel's quantities, in
     //      their unfactored form; values agree with the kernel's to rounding) ----
     float hv[9], gv[9], fv[9];
-    load_lattice_f32(A.pops + PLANE_H * Q, Q, ip, hv);
-    load_lattice_f32(A.pops + PLANE_G * Q, Q, ip, gv);
+    {
+      float2 hg[9];
+      load_hg_f32(A.pops, Q, ip, hg);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        hv[a] = hg[a].x;
+        gv[a] = hg[a].y;
+      }
+    }
     if (FLOW) {
-      load_lattice_f32(A.pops + PLANE_F * Q, Q, ip, fv);
+      load_lattice_f32(A.pops + 18 * Q, Q, ip, fv);
     } else {
 #pragma unroll
       for (int a = 0; a < 9; ++a) fv[a] = 0.0f;
@@ -166,7 +173,7 @@ __global__ void __launch_bounds__(256, 3) adj_collide_kernel(const Consts C, con
       const float hhat = __ldg(A.pb_in + (PLANE_H + a) * Q + jp) +
                          __ldg(A.Phib_in + (long long)ys * PI + xs);
       Ab[a] = hhat;
-      Bb += hhat * __ldg(A.pops + PLANE_H * Q + f32_index(Q, jp, a));
+      Bb += hhat * __ldg(A.pops + f32_pop_index(Q, jp, 0, a));
       Gb[a] = __ldg(A.pb_in + (PLANE_G + a) * Q + jp);
       Fb[a] = FLOW ? __ldg(A.pb_in + (PLANE_F + a) * Q + jp) : 0.0f;
     }
@@ -388,9 +395,14 @@ __global__ void __launch_bounds__(256) adj_init_kernel(const Consts C, const Ini
     const float gy = kW1 * (P(x, yp) - P(x, ym)) + kW2 * ((P(xp, yp) - P(xp, ym)) +
                                                           (P(xm, yp) - P(xm, ym)));
     float gv[9], fv[9], hb[9], gbv[9], fbv[9];
-    load_lattice_f32(A.pops + PLANE_G * Q, Q, ip, gv);
+    {
+      float2 hg[9];
+      load_hg_f32(A.pops, Q, ip, hg);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) gv[a] = hg[a].y;
+    }
     if (FLOW) {
-      load_lattice_f32(A.pops + PLANE_F * Q, Q, ip, fv);
+      load_lattice_f32(A.pops + 18 * Q, Q, ip, fv);
     } else {
 #pragma unroll
       for (int a = 0; a < 9; ++a) fv[a] = 0.0f;

@@ -3,16 +3,17 @@
 // equilibrium initialisation, the moment export and the FP64 reductions.
 //
 // State layout in HBM (one allocation per buffer, row pitch padded to 32 elements):
-//   populations: three lattice regions [h | g | f], each 9 [ny][pitch] planes long, two
-//                buffers (the pull reads one and writes the other). Within a region the
-//                populations are node-interleaved (load9/store9 below): FP32 keeps directions
-//                1..4 and 5..8 of a node as two float4 and the rest population as a float;
-//                16-bit storage keeps the 8 deviations of a node as one 16-byte vector;
+//   populations: 27 planes of pstride elements, two buffers (the pull reads one and writes
+//                the other), node-interleaved (load_hg_f32 and friends below). FP32 keeps the
+//                phase-field and vapour populations of a node paired, (h_a, g_a), in four
+//                float4 and a float2 (planes 0..17), and the flow populations as two float4
+//                and a float (planes 18..26); 16-bit storage keeps the 8 deviations of a node
+//                and lattice as one 16-byte vector in each of the regions [h | g | f];
 //   phi:         three rotating [ny][pitch] float planes holding phi^{n-1}, phi^n, phi^{n+1}
 //                (phi^n feeds the E4 gradient with a two-node halo, phi^{n-1} the d(phi)/dt
 //                of the vapour source, phi^{n+1} = sum h^{n+1} is written by the step).
-// Population q of node (x, y) is at q * pstride + y * rstride + x; the exported layout
-// [q][ny][nx] uses the same formula with pstride = nx ny, rstride = nx.
+// Node (x, y) is node index y * rstride + x; the exported layout [q][ny][nx] puts population q
+// of that node at q * nx ny + y * nx + x.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -160,23 +161,54 @@ template <> struct Storage<BF16> {
   }
 };
 
-// Addressing of the populations. Lattice L (0 h, 1 g, 2 f) owns 9 planes of pstride
-// elements, starting at element 9 L pstride of the buffer; node = y * rstride + x. Within it:
-//   F32: directions 1..4 of the node as one float4 at element 4 node, directions 5..8 as one
-//     float4 at 4 pstride + 4 node, the rest population at 8 pstride + node;
-//   F16 / BF16: the 8 deviations a = 1..8 of the node at 8 node + (a - 1), the rest population
-//     not stored;
-//   F32P (diagnostics of caller-owned exports only): population a at a pstride + node.
-// Every vector is 16-byte aligned because the pitch is a multiple of 32 elements; a warp's 32
-// nodes move as 512 contiguous bytes per vector.
+// Addressing of the populations, with Q = pstride and node = y * rstride + x.
+//   F32: the phase-field and vapour populations in pairs (h_a, g_a): directions 1, 2 of the
+//     node as one float4 (h_1, g_1, h_2, g_2) at element 4 node, directions 3, 4 at
+//     4 Q + 4 node, 5, 6 at 8 Q + 4 node, 7, 8 at 12 Q + 4 node, the rest pair (h_0, g_0) as a
+//     float2 at 16 Q + 2 node; the flow populations from element 18 Q: directions 1..4 as one
+//     float4 at 4 node, 5..8 at 4 Q + 4 node, the rest population at 8 Q + node;
+//   F16 / BF16: lattice L (0 h, 1 g, 2 f) owns elements 9 L Q .. 9 (L + 1) Q; the 8
+//     deviations a = 1..8 of the node at 8 node + (a - 1), the rest population not stored;
+//   F32P (diagnostics of caller-owned exports only): population a of lattice L at
+//     (9 L + a) Q + node.
+// Every vector is aligned to its size because the pitch is a multiple of 32 elements; a
+// warp's 32 nodes move as contiguous 256- or 512-byte runs per vector.
 
-// Index of population a of a node within an FP32 lattice region.
-__device__ __forceinline__ long long f32_index(long long pstride, long long node, int a) {
-  return a == 0 ? 8 * pstride + node
-                : (a < 5 ? 4 * node + (a - 1) : 4 * pstride + 4 * node + (a - 5));
+// Element offset of population a of lattice L at a node within an FP32 buffer.
+__device__ __forceinline__ long long f32_pop_index(long long Q, long long node, int L, int a) {
+  if (L == 2)
+    return 18 * Q + (a == 0 ? 8 * Q + node : (a < 5 ? 4 * node + (a - 1) : 4 * Q + 4 * node + (a - 5)));
+  if (a == 0) return 16 * Q + 2 * node + L;
+  return 4 * Q * ((a - 1) >> 1) + 4 * node + 2 * ((a - 1) & 1) + L;
 }
 
-// The 9 FP32 populations of one lattice region at a node.
+// The phase-field and vapour populations of an FP32 node as pairs hg[a] = (h_a, g_a).
+__device__ __forceinline__ void load_hg_f32(const float* __restrict__ pops, long long Q,
+                                            long long node, float2* hg) {
+  if (!in_range(node, Q, OOB_POPS)) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) hg[a] = make_float2(0.0f, 0.0f);
+    return;
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(pops + 4 * p * Q + 4 * node));
+    hg[2 * p + 1] = make_float2(v.x, v.y);
+    hg[2 * p + 2] = make_float2(v.z, v.w);
+  }
+  hg[0] = __ldg(reinterpret_cast<const float2*>(pops + 16 * Q + 2 * node));
+}
+__device__ __forceinline__ void store_hg_f32(float* __restrict__ pops, long long Q,
+                                             long long node, const float2* hg) {
+  if (!in_range(node, Q, OOB_POPS)) return;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+    *reinterpret_cast<float4*>(pops + 4 * p * Q + 4 * node) =
+        make_float4(hg[2 * p + 1].x, hg[2 * p + 1].y, hg[2 * p + 2].x, hg[2 * p + 2].y);
+  *reinterpret_cast<float2*>(pops + 16 * Q + 2 * node) = hg[0];
+}
+
+// The 9 FP32 flow populations at a node; lat points at the flow region (element 18 Q).
 __device__ __forceinline__ void load_lattice_f32(const float* __restrict__ lat, long long pstride,
                                                  long long node, float* out) {
   if (!in_range(node, pstride, OOB_POPS)) {
@@ -251,7 +283,12 @@ __device__ __forceinline__ void load9(const typename Storage<S>::T* __restrict__
 #pragma unroll
     for (int a = 0; a < 9; ++a) out[a] = __ldg(pops + (9 * L + a) * pstride + node);
   } else if constexpr (!Storage<S>::DEV) {
-    load_lattice_f32(pops + 9 * L * pstride, pstride, node, out);
+    if (L == 2) {
+      load_lattice_f32(pops + 18 * pstride, pstride, node, out);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) out[a] = __ldg(pops + f32_pop_index(pstride, node, L, a));
+    }
   } else {
     decode9<S>(__ldg(reinterpret_cast<const uint4*>(pops + 9 * L * pstride + 8 * node)), M, out);
   }
@@ -267,7 +304,12 @@ __device__ __forceinline__ void store9(typename Storage<S>::T* __restrict__ pops
 #pragma unroll
     for (int a = 0; a < 9; ++a) pops[(9 * L + a) * pstride + node] = p[a];
   } else if constexpr (!Storage<S>::DEV) {
-    store_lattice_f32(pops + 9 * L * pstride, pstride, node, p);
+    if (L == 2) {
+      store_lattice_f32(pops + 18 * pstride, pstride, node, p);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) pops[f32_pop_index(pstride, node, L, a)] = p[a];
+    }
   } else {
     float d[8];
 #pragma unroll
@@ -341,6 +383,14 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return fma(a, b, c); }
+
+// Packed FP32 pairs (sm_100 family): each operation rounds both lanes to nearest exactly as
+// its scalar counterpart would, and issues once for the two lanes.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pair(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
 
 // Isotropic gradient with the stencil of the run (Sec. 3.1.1): E2 is the central difference;
 // E4, E6, E8 sum w(|c|^2) phi(x + c) c over the neighbour shells of Table 1 with the printed

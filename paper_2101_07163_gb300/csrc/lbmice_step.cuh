@@ -1,18 +1,25 @@
-// The fused collide-stream kernel: one launch advances h, g and f by one time step
+// The fused collide-stream step: one launch advances h, g and f by one time step
 // (arXiv 2101.07163, Sec. 2.2.1-2.2.3) over the whole grid.
 //
-// Each CTA owns a TX x TY tile of destination nodes and works in three phases:
-//   A. phi^n of the tile plus a two-node halo (ghosts resolved) -> shared memory;
-//   B. every source node of the tile plus a one-node halo is collided once: moments, the
-//      E4 gradient from the shared phi tile, a_s and the anisotropic flux, the drag, and the
-//      27 post-collision populations, which go to shared memory (h already divided by
-//      a_s^2, together with 1 - 1/a_s^2, so the pull of Eq. (d) is one FMA). Interior nodes
-//      keep their own pre-collision h in registers;
-//   C. each destination pulls its 27 populations from the shared tile, applies Eq. (d),
+// Every kernel here works in three phases per group of destination nodes:
+//   A. phi^n around the group (ghosts resolved) -> shared memory, while each thread's own
+//      populations are loaded into registers;
+//   B. every source node the group pulls from is collided once: moments, the gradient of phi
+//      from the shared tile, a_s and the anisotropic flux, the drag, and the 27 post-collision
+//      populations, which go to shared memory (h already divided by a_s^2 and paired with g,
+//      plus B = 1 - 1/a_s^2, so the pull of Eq. (d) is one FMA);
+//   C. each destination pulls its 27 populations from shared memory, applies Eq. (d), and
 //      writes h, g, f and phi^{n+1} = sum h to HBM.
-// Global loads and stores of phases B and C are row-coalesced (consecutive threads own
-// consecutive x). HBM traffic per node: 27 populations in and out, phi^n, phi^{n-1} in,
-// phi^{n+1} out; halo re-reads hit L2.
+// Two ways of grouping the destinations:
+//   - march_kernel (the default E4 six-fold scheme): a CTA of 8 warps walks up a segment of a
+//     strip of 32 columns, 8 rows per pass; warp w collides the 32 nodes of one row and pulls
+//     the 30 inner ones. Rows collided in one pass stay in a ring of shared rows for the next,
+//     so the only nodes collided twice are the strip's two edge columns (1/15 of the work)
+//     and two rows where a segment starts.
+//   - step_kernel: one CTA per TX x TY tile, which collides its tile plus a one-node ring
+//     (used for the wider stencils, and as alternative shapes of the batched launch).
+// HBM traffic per node: 27 populations in and out, phi^n, phi^{n-1} in, phi^{n+1} out; the
+// re-read edge columns and rows hit L2.
 #pragma once
 
 #include <type_traits>
@@ -34,6 +41,26 @@ struct StepPtrs {
   float* __restrict__ rho_np1;
 };
 
+// Collided populations of SN source nodes in shared memory: (h*_a / a_s^2, g*_a) pairs,
+// f*_a, and B = 1 - 1/a_s^2 of every source node.
+struct PostTile {
+  float2* hg;  // [9][SN]
+  float* f;    // [9][SN] (flow only)
+  float* B;    // [SN]
+  int SN;
+  template <bool FLOW>
+  __host__ __device__ static constexpr size_t floats(int SN) { return (size_t)SN * (FLOW ? 28 : 19); }
+  template <bool FLOW>
+  __device__ static PostTile at(float* base, int SN) {
+    PostTile T;
+    T.hg = reinterpret_cast<float2*>(base);
+    T.f = base + 18 * SN;
+    T.B = T.f + (FLOW ? 9 * SN : 0);
+    T.SN = SN;
+    return T;
+  }
+};
+
 // Tile of TX x TY destination nodes for a gradient stencil of radius R (1: the default E4
 // with six-fold anisotropy, specialised; 2: any stencil up to E8 and either fold): the phi
 // tile has a halo of R + 1 (the stencil around every ring node), the collided source tile a
@@ -49,67 +76,18 @@ struct Tile {
   static constexpr int NT = TX * TY;
   template <bool FLOW>
   static constexpr size_t smem_bytes() {
-    return sizeof(float) * (size_t)(PN + (FLOW ? 27 : 18) * SN + SN);
+    return sizeof(float) * (PostTile::floats<FLOW>(SN) + PN);
   }
 };
 
-// Per-node coefficients of the three collisions, so that each direction costs a few FMAs:
-//   phase field, Eq. (d)/(e): h* = h - (h - h^eq)/eta + w Q dt/tau0, h^eq = w (phi - 3 Dphi
-//     c.N), stored divided by a_s^2:  h*/a_s^2 = a1 h + w (a2 - a3 c.N);
-//   vapour: g* = g - (g - g^eq)/tau_g + w S dt, g^eq = w U (1 + 3 c.u*):
-//     g* = b1 g + w (b2 + b3 c.u*);
-//   flow: BGK to the second-order f^eq(rho, u*) plus Guo forcing of F = -k u*:
-//     f* = c1 f + w (c2 + c.u* (c3 + c4 c.u*) + c.F (c5 + c6 c.u*)).
-// Every product and sum is an explicit fmaf or round-to-nearest operation: the compiler may
-// not contract them differently in different kernels, so every kernel that collides a node
-// (single-grid or batched) produces the same bits.
-template <bool FLOW>
-struct FactoredCollision {
-  float a1, a2, a3, b1, b2, b3, ux, uy;
-  float c1 = 0.0f, c2 = 0.0f, c3 = 0.0f, c4 = 0.0f, c5 = 0.0f, c6 = 0.0f, Fx = 0.0f, Fy = 0.0f;
-  __device__ __forceinline__ FactoredCollision(const Consts& C, float ph, float U, float rho,
-                                               float inv_as2, float inv_eta, float srcQ,
-                                               float inv_tg, float srcU, float k, float usx,
-                                               float usy)
-      : ux(usx), uy(usy) {
-    a1 = __fmul_rn(1.0f - inv_eta, inv_as2);
-    a2 = __fmul_rn(fmaf(ph, inv_eta, srcQ), inv_as2);
-    a3 = __fmul_rn(__fmul_rn(C.Dphi3, inv_eta), inv_as2);
-    b1 = 1.0f - inv_tg;
-    b2 = fmaf(U, inv_tg, srcU);
-    b3 = __fmul_rn(__fmul_rn(3.0f, U), inv_tg);
-    if (FLOW) {
-      Fx = -__fmul_rn(k, usx);
-      Fy = -__fmul_rn(k, usy);
-      const float uF = fmaf(usx, Fx, __fmul_rn(usy, Fy));
-      const float uu = fmaf(usx, usx, __fmul_rn(usy, usy));
-      const float r = __fmul_rn(rho, C.inv_tau_f);
-      c1 = 1.0f - C.inv_tau_f;
-      c2 = fmaf(r, fmaf(-1.5f, uu, 1.0f), -__fmul_rn(__fmul_rn(3.0f, C.guo), uF));
-      c3 = __fmul_rn(3.0f, r);
-      c4 = __fmul_rn(4.5f, r);
-      c5 = __fmul_rn(3.0f, C.guo);
-      c6 = __fmul_rn(9.0f, C.guo);
-    }
-  }
-  // Populations given as deviations d_a = p_a - w_a M from the moments (phi, U, rho): each
-  // collision is affine in p_a with slope a1, b1 or c1, so adding slope x M to the constant
-  // term gives the same collided populations from the deviations.
-  __device__ __forceinline__ void shift(float Mh, float Mg, float Mf) {
-    a2 = fmaf(a1, Mh, a2);
-    b2 = fmaf(b1, Mg, b2);
-    if (FLOW) c2 = fmaf(c1, Mf, c2);
-  }
-  __device__ __forceinline__ float h(int a, float hv, float Nx, float Ny) const {
-    return fmaf(hv, a1, __fmul_rn(w_of(a), fmaf(-a3, cdot(a, Nx, Ny), a2)));
-  }
-  __device__ __forceinline__ float g(int a, float gv) const {
-    return fmaf(gv, b1, __fmul_rn(w_of(a), fmaf(b3, cdot(a, ux, uy), b2)));
-  }
-  __device__ __forceinline__ float f(int a, float fv) const {
-    const float cu = cdot(a, ux, uy);
-    const float t = fmaf(fmaf(c4, cu, c3), cu, c2);
-    return fmaf(fv, c1, __fmul_rn(w_of(a), fmaf(cdot(a, Fx, Fy), fmaf(c6, cu, c5), t)));
+// phi around the node a collision is taken at, in the 2D tile: v(dx, dy) = phi at the
+// offset; pc is the centre's index in the tile.
+struct TileView {
+  const float* s;
+  int pc, PW, PN, R;
+  __device__ __forceinline__ float operator()(int dx, int dy) const { return s[pc + dy * PW + dx]; }
+  __device__ __forceinline__ bool ok() const {
+    return in_range(pc - R * (PW + 1), PN, OOB_SHARED) && in_range(pc + R * (PW + 1), PN, OOB_SHARED);
   }
 };
 
@@ -121,7 +99,8 @@ struct OwnIn;
 template <class S, bool FLOW>
 struct OwnIn<S, FLOW, false> {
   bool valid;
-  float h[9], g[9], f[9], php;
+  float2 hg[9];
+  float f[9], php;
 };
 template <class S, bool FLOW>
 struct OwnIn<S, FLOW, true> {
@@ -134,16 +113,15 @@ template <class S, bool FLOW>
 __device__ __forceinline__ void own_load(const Consts& C, const StepPtrs& P, int X, int Y,
                                          OwnIn<S, FLOW>& in) {
   using ST = Storage<S>;
-  in.valid = X < C.nx && Y < C.ny;
+  in.valid = X >= 0 && Y >= 0 && X < C.nx && Y < C.ny;
   if (!in.valid) return;
   const long long idx = (long long)Y * C.pitch + X;
   const long long nd = (long long)Y * C.rstride + X;
   const typename ST::T* __restrict__ pops = static_cast<const typename ST::T*>(P.pin);
   const long long np = (long long)C.pitch * C.ny;
   if constexpr (!ST::DEV) {
-    load_lattice_f32(pops + PLANE_H * C.pstride, C.pstride, nd, in.h);
-    load_lattice_f32(pops + PLANE_G * C.pstride, C.pstride, nd, in.g);
-    if (FLOW) load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, in.f);
+    load_hg_f32(pops, C.pstride, nd, in.hg);
+    if (FLOW) load_lattice_f32(pops + 18 * C.pstride, C.pstride, nd, in.f);
   } else {
     in.h = ldg_vec(reinterpret_cast<const uint4*>(pops), nd, C.pstride);
     in.g = ldg_vec(reinterpret_cast<const uint4*>(pops + 9 * C.pstride), nd, C.pstride);
@@ -156,20 +134,56 @@ __device__ __forceinline__ void own_load(const Consts& C, const StepPtrs& P, int
   in.php = ldg_plane(P.phi_nm1, idx, np);
 }
 
-// Collide the source node at tile position (sx, sy) in [0, TX+2) x [0, TY+2), global
-// coordinates (X, Y) in [-1, nx] x [-1, ny], and store its post-collision populations.
-// Ghost positions take the collision of the node their face rule maps them to (directions
-// mirrored across a free-slip wall), or the fixed inlet state.
-template <int TX, int TY, bool FLOW, class S, bool OWN, int R>
+// Deviations (d^h_a, d^g_a) of a node from its two 16-bit vectors; the rest pair is minus the
+// sum of the others (summed in the pairing of sum9).
+template <class S>
+__device__ __forceinline__ void deviations_hg(uint4 vh, uint4 vg, float2* hg) {
+  float dh[8], dg[8];
+  Storage<S>::unpack8(vh, dh);
+  Storage<S>::unpack8(vg, dg);
+#pragma unroll
+  for (int a = 1; a < 9; ++a) hg[a] = pair(dh[a - 1], dg[a - 1]);
+  const float2 s = fadd2(fadd2(fadd2(hg[1], hg[3]), fadd2(hg[2], hg[4])),
+                         fadd2(fadd2(hg[5], hg[7]), fadd2(hg[6], hg[8])));
+  hg[0] = pair(-s.x, -s.y);
+}
+
+// sum9 of pairs, lane by lane, in the same grouping as sum9.
+__device__ __forceinline__ float2 sum9_2(const float2* v) {
+  return fadd2(v[0], fadd2(fadd2(fadd2(v[1], v[3]), fadd2(v[2], v[4])),
+                           fadd2(fadd2(v[5], v[7]), fadd2(v[6], v[8]))));
+}
+
+// Collide the source node at global coordinates (X, Y) in [-1, nx] x [-1, ny] and store its
+// post-collision populations in slot `node` of the shared tile T. view_at(sx, sy) returns the
+// phi view (operator()(dx, dy), ok()) centred on the tile position of this node shifted by
+// (sx, sy): a ghost node of a non-periodic face takes the collision of the interior node its
+// face rule maps it to (directions mirrored across a free-slip wall), or the fixed inlet
+// state. OWN: the node is the thread's destination; its pre-collision h (as populations) goes
+// to hown, for the pull of Eq. (d), and its loads may come from pre.
+//
+// The collision, Sec. 2.2.1-2.2.3, is evaluated in a factored form with per-node
+// coefficients (every product and sum an explicit round-to-nearest operation, so every kernel
+// that collides a node produces the same bits):
+//   phase field, Eq. (d)/(e): h* = h - (h - h^eq)/eta + w Q dt/tau0, h^eq = w (phi - 3 Dphi
+//     c.N), stored divided by a_s^2:  h*/a_s^2 = a1 h + w (a2 - a3 c.N);
+//   vapour: g* = g - (g - g^eq)/tau_g + w S dt, g^eq = w U (1 + 3 c.u*):
+//     g* = b1 g + w (b2 + b3 c.u*);
+//   flow: BGK to the second-order f^eq(rho, u*) plus Guo forcing of F = -k u*; since c.F =
+//     -k c.u*, f* = c1 f + w (c2 + c3 c.u* + c4 (c.u*)^2) with
+//     c2 = r (1 - 3/2 u*.u*) + 3 gamma k u*.u*, c3 = 3 (r - gamma k), c4 = 9/2 (r - 2 gamma k),
+//     r = rho / tau_f, gamma = 1 - 1/(2 tau_f).
+// h and g are evaluated as pairs (h_a, g_a) with packed FP32x2 operations, f as pairs of
+// directions; opposite directions use exactly negated odd terms, and the weights 1/36 and
+// 4/9 are the weight 1/9 scaled by powers of two, so mirror images of a state stay
+// bit-exact mirror images.
+template <bool FLOW, class S, bool OWN, int R, class ViewAt>
 __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& P, int X, int Y,
-                                               int sx, int sy, const float* __restrict__ sphi,
-                                               float* __restrict__ spost,
-                                               float* __restrict__ sB, float* hown,
+                                               int node, const ViewAt& view_at,
+                                               const PostTile& T, float* hown,
                                                const OwnIn<S, FLOW>* pre = nullptr) {
-  using T = Tile<TX, TY, R>;
-  const int node = sy * T::SW + sx;
-  if (!in_range(node, T::SN, OOB_SHARED)) return;
-  int mx = X, my = Y, lx = sx, ly = sy;
+  if (!in_range(node, T.SN, OOB_SHARED)) return;
+  int mx = X, my = Y, shx = 0, shy = 0;
   bool mirx = false, miry = false;
   int inlet = -1;
   if (X < 0 || X >= C.nx) {
@@ -179,7 +193,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
       mx = X < 0 ? X + C.nx : X - C.nx;
     } else {
       mx = X < 0 ? 0 : C.nx - 1;
-      lx += X < 0 ? 1 : -1;
+      shx = X < 0 ? 1 : -1;
       mirx = bc == BC_FREESLIP;
       if (bc == BC_INLET) inlet = face;
     }
@@ -191,7 +205,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
       my = Y < 0 ? Y + C.ny : Y - C.ny;
     } else {
       my = Y < 0 ? 0 : C.ny - 1;
-      ly += Y < 0 ? 1 : -1;
+      shy = Y < 0 ? 1 : -1;
       miry = bc == BC_FREESLIP;
       if (bc == BC_INLET && inlet < 0) inlet = face;
     }
@@ -200,6 +214,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   const long long idx = (long long)my * C.pitch + mx;
   const typename ST::T* __restrict__ pops = static_cast<const typename ST::T*>(P.pin);
   const long long nd = (long long)my * C.rstride + mx;
+  const int SN = T.SN;
 
   if (inlet >= 0) {
     // Inlet ghost: vapour at the inlet state, flow equilibrium at the adjacent density.
@@ -213,7 +228,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
         rho = ldg_plane(P.rho_n, idx, (long long)C.pitch * C.ny);
       } else {
         float fv[9];
-        load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, fv);
+        load_lattice_f32(pops + 18 * C.pstride, C.pstride, nd, fv);
         rho = sum9(fv);
       }
     }
@@ -221,38 +236,32 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const float cu = cdot(a, ux, uy);
-      spost[(PLANE_H + a) * T::SN + node] = -w_of(a);
-      spost[(PLANE_G + a) * T::SN + node] = w_of(a) * C.U_in * (1.0f + 3.0f * cu);
-      if (FLOW)
-        spost[(PLANE_F + a) * T::SN + node] =
-            w_of(a) * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+      T.hg[a * SN + node] = pair(-w_of(a), w_of(a) * C.U_in * (1.0f + 3.0f * cu));
+      if (FLOW) T.f[a * SN + node] = w_of(a) * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
     }
-    sB[node] = 0.0f;
+    T.B[node] = 0.0f;
     return;
   }
 
+  const auto V = view_at(shx, shy);
+  if (!V.ok()) return;
   // ---- populations and moments at time n (Sec. 2.2) ----
-  const int pc = (ly + R) * T::PW + (lx + R);
-  if (!in_range(pc - R * (T::PW + 1), T::PN, OOB_SHARED) ||
-      !in_range(pc + R * (T::PW + 1), T::PN, OOB_SHARED))
-    return;
-  const float ph = sphi[pc];
+  const float ph = V(0, 0);
   // FP32: the populations. 16-bit: their deviations d_a = p_a - w_a M from the stored
   // moments M (phi, U, rho), with d_0 = -sum_{a>0} d_a; the moments are the stored ones and
   // the momentum is sum c_a d_a (the w_a M terms cancel exactly).
-  float hv[9], gv[9], fv[9];
+  float2 hg[9];
+  float fv[9];
   float php, U, rho = 1.0f;
   if (OWN && pre && pre->valid) {  // loaded before the phi tile's barrier
     if constexpr (!ST::DEV) {
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        hv[a] = pre->h[a];
-        gv[a] = pre->g[a];
+        hg[a] = pre->hg[a];
         if (FLOW) fv[a] = pre->f[a];
       }
     } else {
-      deviations9<S>(pre->h, hv);
-      deviations9<S>(pre->g, gv);
+      deviations_hg<S>(pre->h, pre->g, hg);
       U = pre->U;
       if (FLOW) {
         deviations9<S>(pre->f, fv);
@@ -262,14 +271,13 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     php = pre->php;
   } else {
     if constexpr (!ST::DEV) {
-      load_lattice_f32(pops + PLANE_H * C.pstride, C.pstride, nd, hv);
-      load_lattice_f32(pops + PLANE_G * C.pstride, C.pstride, nd, gv);
-      if (FLOW) load_lattice_f32(pops + PLANE_F * C.pstride, C.pstride, nd, fv);
+      load_hg_f32(pops, C.pstride, nd, hg);
+      if (FLOW) load_lattice_f32(pops + 18 * C.pstride, C.pstride, nd, fv);
     } else {
       const uint4* pv = reinterpret_cast<const uint4*>(pops);
       const long long np = (long long)C.pitch * C.ny;
-      deviations9<S>(ldg_vec(pv, nd, C.pstride), hv);
-      deviations9<S>(ldg_vec(pv + (9 * C.pstride) / 8, nd, C.pstride), gv);
+      deviations_hg<S>(ldg_vec(pv, nd, C.pstride), ldg_vec(pv + (9 * C.pstride) / 8, nd, C.pstride),
+                       hg);
       U = ldg_plane(P.U_n, idx, np);
       if (FLOW) {
         deviations9<S>(ldg_vec(pv + (18 * C.pstride) / 8, nd, C.pstride), fv);
@@ -279,7 +287,8 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     php = ldg_plane(P.phi_nm1, idx, (long long)C.pitch * C.ny);
   }
   if constexpr (!ST::DEV) {
-    U = sum9(gv);
+    U = hg[0].y + (((hg[1].y + hg[3].y) + (hg[2].y + hg[4].y)) +
+                   ((hg[5].y + hg[7].y) + (hg[6].y + hg[8].y)));
     if (FLOW) rho = sum9(fv);
   }
   float jx = 0.0f, jy = 0.0f;
@@ -290,16 +299,13 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
 
   // ---- gradient of phi (Sec. 3.1.1, Table 1) and anisotropy (Sec. 2.1) ----
   float gx, gy;
-  if (R == 1) {  // E4 with six-fold anisotropy: the default, with no run-time variant branch
-    const float pE = sphi[pc + 1], pW = sphi[pc - 1];
-    const float pN = sphi[pc + T::PW], pS = sphi[pc - T::PW];
-    const float pNE = sphi[pc + T::PW + 1], pNW = sphi[pc + T::PW - 1];
-    const float pSE = sphi[pc - T::PW + 1], pSW = sphi[pc - T::PW - 1];
+  if constexpr (R == 1) {  // E4 with six-fold anisotropy: the default, with no run-time variant branch
+    const float pE = V(1, 0), pW = V(-1, 0), pN = V(0, 1), pS = V(0, -1);
+    const float pNE = V(1, 1), pNW = V(-1, 1), pSE = V(1, -1), pSW = V(-1, -1);
     gx = fmaf(kW1, pE - pW, __fmul_rn(kW2, (pNE - pNW) + (pSE - pSW)));
     gy = fmaf(kW1, pN - pS, __fmul_rn(kW2, (pNE - pSE) + (pNW - pSW)));
   } else {  // any stencil and fold, chosen at run time, on a phi tile of halo R + 1 = 3
-    gradient_stencil<float>(C.stencil, [&](int dx, int dy) { return sphi[pc + dy * T::PW + dx]; },
-                            gx, gy);
+    gradient_stencil<float>(C.stencil, V, gx, gy);
   }
   // Every product and sum from here to the collision is an explicit fmaf or round-to-nearest
   // operation, like the collision itself: no kernel that collides a node may contract them
@@ -353,91 +359,172 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
 
   if (OWN) {  // the own node's h populations, for the pull of Eq. (d)
 #pragma unroll
-    for (int a = 0; a < 9; ++a) hown[a] = ST::DEV ? fmaf(w_of(a), ph, hv[a]) : hv[a];
+    for (int a = 0; a < 9; ++a) hown[a] = ST::DEV ? fmaf(w_of(a), ph, hg[a].x) : hg[a].x;
   }
-  if constexpr (!Storage<S>::DEV) {
-    // FP32 storage: the factored collision (FactoredCollision), each collided population
-    // stored as it is formed (no staging array: the kernel stays at 64 registers); the
-    // free-slip mirror is a uniform branch, so the common path stores at fixed
-    // shared-memory offsets
-    FactoredCollision<FLOW> fc(C, ph, U, rho, inv_as2, inv_eta, srcQ, inv_tg, srcU, k, usx, usy);
-    auto emit = [&](auto mirrored) {
-      constexpr bool M = decltype(mirrored)::value;
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        int am = a;
-        if constexpr (M) {
-          am = mirx ? mirx_of(a) : a;
-          am = miry ? miry_of(am) : am;
-        }
-        spost[(PLANE_H + am) * T::SN + node] = fc.h(a, hv[a], Nx, Ny);
-        spost[(PLANE_G + am) * T::SN + node] = fc.g(a, gv[a]);
-        if (FLOW) spost[(PLANE_F + am) * T::SN + node] = fc.f(a, fv[a]);
-      }
-    };
-    if (mirx || miry) emit(std::true_type{}); else emit(std::false_type{});
-  } else {
-    // 16-bit storage: the same factored collision applied to the deviations (its constant
-    // terms shifted by the moments), staged in registers, then stored
-    FactoredCollision<FLOW> fc(C, ph, U, rho, inv_as2, inv_eta, srcQ, inv_tg, srcU, k, usx, usy);
-    fc.shift(ph, U, rho);
-    float post[27];
-  #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      post[PLANE_H + a] = fc.h(a, hv[a], Nx, Ny);
-      post[PLANE_G + a] = fc.g(a, gv[a]);
-      if (FLOW) post[PLANE_F + a] = fc.f(a, fv[a]);
-    }
-    constexpr int NQ = FLOW ? 27 : 18;
-    if (!mirx && !miry) {
-  #pragma unroll
-      for (int q = 0; q < NQ; ++q) spost[q * T::SN + node] = post[q];
-    } else {  // ghost behind a free-slip wall: directions mirrored
-  #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        int am = mirx ? mirx_of(q % 9) : q % 9;
+
+  // ---- the collision (factored, packed) ----
+  constexpr float wA = 1.0f / 9.0f;
+  float a2 = __fmul_rn(fmaf(ph, inv_eta, srcQ), inv_as2);
+  float b2 = fmaf(U, inv_tg, srcU);
+  const float a1 = __fmul_rn(1.0f - inv_eta, inv_as2);
+  const float b1 = 1.0f - inv_tg;
+  const float a3 = __fmul_rn(__fmul_rn(C.Dphi3, inv_eta), inv_as2);
+  const float b3 = __fmul_rn(__fmul_rn(3.0f, U), inv_tg);
+  if (ST::DEV) {  // deviations: each collision is affine in p_a, slope a1 (b1) times M moves
+    a2 = fmaf(a1, ph, a2);  // into the constant term
+    b2 = fmaf(b1, U, b2);
+  }
+  const float2 K1 = pair(a1, b1);
+  const float2 EA = pair(__fmul_rn(a2, wA), __fmul_rn(b2, wA));
+  const float2 OA = pair(__fmul_rn(a3, -wA), __fmul_rn(b3, wA));
+  const float2 nOA = pair(__fmul_rn(a3, wA), __fmul_rn(b3, -wA));
+  const float2 V1 = pair(Nx, usx), V2 = pair(Ny, usy);  // (c.N, c.u*) of directions 1, 2
+  const float2 V5 = fadd2(V1, V2);                      // direction 5
+  const float2 V6 = pair(Ny - Nx, usy - usx);           // direction 6
+  const float2 q4 = splat(0.25f);
+  float c1 = 0.0f, c2 = 0.0f, c3 = 0.0f, c4 = 0.0f;
+  if (FLOW) {
+    c1 = 1.0f - C.inv_tau_f;
+    const float r = __fmul_rn(rho, C.inv_tau_f);
+    const float uu = fmaf(usx, usx, __fmul_rn(usy, usy));
+    const float gk = __fmul_rn(C.guo, k);
+    c2 = fmaf(r, fmaf(-1.5f, uu, 1.0f), __fmul_rn(__fmul_rn(3.0f, gk), uu));
+    if (ST::DEV) c2 = fmaf(c1, rho, c2);
+    c3 = __fmul_rn(3.0f, r - gk);
+    c4 = __fmul_rn(4.5f, fmaf(-2.0f, gk, r));
+  }
+  // Each collided value is stored as it is formed (nothing staged: the kernels stay within
+  // their register budgets); behind a free-slip wall the directions are mirrored, a uniform
+  // branch, so the common path stores at fixed shared-memory offsets.
+  const auto form = [&](auto mirrored) {
+    constexpr bool M = decltype(mirrored)::value;
+    const auto slot = [&](int a) {
+      int am = a;
+      if constexpr (M) {
+        am = mirx ? mirx_of(a) : a;
         am = miry ? miry_of(am) : am;
-        spost[(q - q % 9 + am) * T::SN + node] = post[q];
       }
+      return am * SN + node;
+    };
+    T.hg[slot(1)] = ffma2(K1, hg[1], ffma2(OA, V1, EA));
+    T.hg[slot(2)] = ffma2(K1, hg[2], ffma2(OA, V2, EA));
+    T.hg[slot(3)] = ffma2(K1, hg[3], ffma2(nOA, V1, EA));
+    T.hg[slot(4)] = ffma2(K1, hg[4], ffma2(nOA, V2, EA));
+    T.hg[slot(5)] = ffma2(K1, hg[5], fmul2(q4, ffma2(OA, V5, EA)));
+    T.hg[slot(6)] = ffma2(K1, hg[6], fmul2(q4, ffma2(OA, V6, EA)));
+    T.hg[slot(7)] = ffma2(K1, hg[7], fmul2(q4, ffma2(nOA, V5, EA)));
+    T.hg[slot(8)] = ffma2(K1, hg[8], fmul2(q4, ffma2(nOA, V6, EA)));
+    T.hg[slot(0)] = ffma2(K1, hg[0], fmul2(splat(4.0f), EA));
+    if (FLOW) {
+      const float2 C1 = splat(c1);
+      const float2 C2 = splat(__fmul_rn(c2, wA));
+      const float2 C3 = splat(__fmul_rn(c3, wA)), nC3 = splat(__fmul_rn(c3, -wA));
+      const float2 C4 = splat(__fmul_rn(c4, wA));
+      const float2 cuA = pair(usx, usy);    // c.u* of directions 1, 2 (3, 4: negated)
+      const float2 cuD = pair(V5.y, V6.y);  // directions 5, 6 (7, 8: negated)
+      const float2 eA = ffma2(C4, fmul2(cuA, cuA), C2);
+      const float2 f12 = ffma2(C1, pair(fv[1], fv[2]), ffma2(C3, cuA, eA));
+      T.f[slot(1)] = f12.x;
+      T.f[slot(2)] = f12.y;
+      const float2 f34 = ffma2(C1, pair(fv[3], fv[4]), ffma2(nC3, cuA, eA));
+      T.f[slot(3)] = f34.x;
+      T.f[slot(4)] = f34.y;
+      const float2 eD = ffma2(C4, fmul2(cuD, cuD), C2);
+      const float2 f56 = ffma2(C1, pair(fv[5], fv[6]), fmul2(q4, ffma2(C3, cuD, eD)));
+      T.f[slot(5)] = f56.x;
+      T.f[slot(6)] = f56.y;
+      const float2 f78 = ffma2(C1, pair(fv[7], fv[8]), fmul2(q4, ffma2(nC3, cuD, eD)));
+      T.f[slot(7)] = f78.x;
+      T.f[slot(8)] = f78.y;
+      T.f[slot(0)] = fmaf(c1, fv[0], __fmul_rn(4.0f, C2.x));
     }
-  }
-  sB[node] = 1.0f - inv_as2;
+  };
+  if (mirx || miry) form(std::true_type{}); else form(std::false_type{});
+  T.B[node] = 1.0f - inv_as2;
 }
 
-// One TX x TY tile with origin (x0, y0), computed by the TX * TY threads of the CTA (thread
-// tid owns node (x0 + tid % TX, y0 + tid / TX)). smem holds Tile<TX, TY, R>::smem_bytes.
-// PRE: issue the own node's loads before the phi tile's barrier (OwnIn).
-template <int TX, int TY, bool FLOW, class S, int R = 1, bool PRE = true>
-__device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, int x0, int y0,
-                                          float* smem) {
+// The pull of destination (X, Y), Eq. (d) for h: src(a) is the shared slot of the source node
+// y - c_a; writes h, g, f and phi^{n+1} (16-bit storage: U^{n+1}, rho^{n+1} too).
+template <bool FLOW, class S, class SrcOf>
+__device__ __forceinline__ void pull_store(const Consts& C, const StepPtrs& P, int X, int Y,
+                                           const SrcOf& src, const PostTile& T,
+                                           const float* hown) {
   using ST = Storage<S>;
-  using T = Tile<TX, TY, R>;
-  constexpr int H = T::H;
-  float* sphi = smem;
-  float* spost = sphi + T::PN;
-  float* sB = spost + (FLOW ? 27 : 18) * T::SN;
-  const int tid = threadIdx.x;
-  const int tx = tid % TX, ty = tid / TX;
+  const int SN = T.SN;
+  const long long idx = (long long)Y * C.pitch + X;
+  const long long np = (long long)C.pitch * C.ny;
+  const long long nd = (long long)Y * C.rstride + X;
+  float2 hg[9];
+  float fn[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const int s = src(a);
+    float2 v = T.hg[a * SN + s];
+    v.x = fmaf(hown[a], T.B[s], v.x);
+    hg[a] = v;
+    if (FLOW) fn[a] = T.f[a * SN + s];
+  }
+  if constexpr (!ST::DEV) {
+    float* __restrict__ po = static_cast<float*>(P.pout);
+    store_hg_f32(po, C.pstride, nd, hg);
+    if (FLOW) store_lattice_f32(po + 18 * C.pstride, C.pstride, nd, fn);
+    const float phin = hg[0].x + (((hg[1].x + hg[3].x) + (hg[2].x + hg[4].x)) +
+                                  ((hg[5].x + hg[7].x) + (hg[6].x + hg[8].x)));
+    st_plane(P.phi_np1, idx, np, phin);
+  } else {
+    // 16-bit storage: the moments of the pulled populations are stored in FP32 and the
+    // moving populations as deviations d_a = p_a - w_a M from them
+    const float2 m = sum9_2(hg);  // (phi^{n+1}, U^{n+1})
+    st_plane(P.phi_np1, idx, np, m.x);
+    st_plane(P.U_np1, idx, np, m.y);
+    float dh[8], dg[8];
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+      const float2 d = ffma2(splat(-w_of(a)), m, hg[a]);
+      dh[a - 1] = d.x;
+      dg[a - 1] = d.y;
+    }
+    typename ST::T* __restrict__ pout = static_cast<typename ST::T*>(P.pout);
+    if (in_range(nd, C.pstride, OOB_POPS)) {
+      reinterpret_cast<uint4*>(pout)[nd] = ST::pack8(dh);
+      reinterpret_cast<uint4*>(pout + 9 * C.pstride)[nd] = ST::pack8(dg);
+    }
+    if (FLOW) {
+      const float rn = sum9(fn);
+      st_plane(P.rho_np1, idx, np, rn);
+      float df[8];
+#pragma unroll
+      for (int a = 1; a < 9; a += 2) {
+        const float2 d = ffma2(splat(-w_of(a)), splat(rn), pair(fn[a], fn[a + 1]));
+        df[a - 1] = d.x;
+        df[a] = d.y;
+      }
+      if (in_range(nd, C.pstride, OOB_POPS))
+        reinterpret_cast<uint4*>(pout + 18 * C.pstride)[nd] = ST::pack8(df);
+    }
+  }
+}
 
-  // the own node's populations, in flight while the phi tile loads
-  OwnIn<S, FLOW> own;
-  if (PRE) own_load<S, FLOW>(C, P, x0 + tx, y0 + ty, own);
-  else own.valid = false;
-
-  // ---- A: phi^n with a halo of H = R + 1 nodes ----
-  if (x0 >= H && y0 >= H && x0 + TX + H <= C.nx && y0 + TY + H <= C.ny) {
+// phi^n of a tile with origin (x0, y0) and a halo of H nodes into sphi (PW x PH values),
+// ghosts resolved (beyond the grid's halo of R: 0, never read).
+template <int PW, int PH>
+__device__ __forceinline__ void load_phi_tile(const Consts& C, const StepPtrs& P, int x0, int y0,
+                                              int H, int R, float* sphi, int tid, int nthreads) {
+  constexpr int PN = PW * PH;
+  if (x0 >= H && y0 >= H && x0 - H + PW <= C.nx && y0 - H + PH <= C.ny) {
     // the halo lies inside the grid (almost every tile): no ghost resolution
     const float* __restrict__ pb = P.phi_n + (long long)(y0 - H) * C.pitch + (x0 - H);
     const int pitch = (int)C.pitch;
-    for (int i = tid; i < T::PN; i += T::NT) {
-      const int lx = i % T::PW, ly = i / T::PW;
+    for (int i = tid; i < PN; i += nthreads) {
+      const int lx = i % PW, ly = i / PW;
       if (in_range((long long)(y0 - H + ly) * C.pitch + (x0 - H + lx),
                    (long long)C.pitch * C.ny, OOB_PLANE))
         sphi[i] = __ldg(pb + ly * pitch + lx);
     }
-  } else
-  for (int i = tid; i < T::PN; i += T::NT) {
-    const int lx = i % T::PW, ly = i / T::PW;
+    return;
+  }
+  for (int i = tid; i < PN; i += nthreads) {
+    const int lx = i % PW, ly = i / PW;
     const int X = x0 - H + lx, Y = y0 - H + ly;
     int gx, gy;
     float v = -1.0f;
@@ -449,15 +536,41 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
     }
     sphi[i] = v;
   }
+}
+
+// One TX x TY tile with origin (x0, y0), computed by the TX * TY threads of the CTA (thread
+// tid owns node (x0 + tid % TX, y0 + tid / TX)). smem holds Tile<TX, TY, R>::smem_bytes.
+// PRE: issue the own node's loads before the phi tile's barrier (OwnIn).
+template <int TX, int TY, bool FLOW, class S, int R = 1, bool PRE = true>
+__device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, int x0, int y0,
+                                          float* smem) {
+  using T = Tile<TX, TY, R>;
+  const PostTile post = PostTile::at<FLOW>(smem, T::SN);
+  float* sphi = smem + PostTile::floats<FLOW>(T::SN);
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+
+  // the own node's populations, in flight while the phi tile loads
+  OwnIn<S, FLOW> own;
+  if (PRE) own_load<S, FLOW>(C, P, x0 + tx, y0 + ty, own);
+  else own.valid = false;
+
+  // ---- A: phi^n with a halo of H = R + 1 nodes ----
+  load_phi_tile<T::PW, TY + 2 * T::H>(C, P, x0, y0, T::H, R, sphi, tid, T::NT);
   __syncthreads();
 
   // ---- B: collide the tile (own node per thread) and its one-node ring ----
   float hown[9];
+  auto view_of = [&](int sx, int sy) {
+    return [=](int shx, int shy) {
+      return TileView{sphi, (sy + shy + R) * T::PW + (sx + shx + R), T::PW, T::PN, R};
+    };
+  };
   {
     const int X = x0 + tx, Y = y0 + ty;
     if (X <= C.nx && Y <= C.ny)
-      collide_source<TX, TY, FLOW, S, true, R>(C, P, X, Y, tx + 1, ty + 1, sphi, spost, sB,
-                                               hown, &own);
+      collide_source<FLOW, S, true, R>(C, P, X, Y, (ty + 1) * T::SW + tx + 1,
+                                       view_of(tx + 1, ty + 1), post, hown, &own);
   }
   for (int r = tid; r < T::NRING; r += T::NT) {
     // ring order: bottom row, top row, then left and right columns
@@ -467,89 +580,213 @@ __device__ __forceinline__ void step_tile(const Consts& C, const StepPtrs& P, in
     else { const int k = r - 2 * T::SW; sy = 1 + (k >> 1); sx = (k & 1) ? TX + 1 : 0; }
     const int X = x0 - 1 + sx, Y = y0 - 1 + sy;
     if (X >= -1 && X <= C.nx && Y >= -1 && Y <= C.ny)
-      collide_source<TX, TY, FLOW, S, false, R>(C, P, X, Y, sx, sy, sphi, spost, sB, nullptr);
+      collide_source<FLOW, S, false, R>(C, P, X, Y, sy * T::SW + sx, view_of(sx, sy), post,
+                                        nullptr);
   }
   __syncthreads();
 
   // ---- C: pull, Eq. (d) for h, write populations and phi^{n+1} ----
   const int X = x0 + tx, Y = y0 + ty;
   if (X >= C.nx || Y >= C.ny) return;  // (this thread has no node in this tile)
-  const long long idx = (long long)Y * C.pitch + X;
-  const long long np = (long long)C.pitch * C.ny;
   // the nine pull sources span tile positions ty..ty+2 x tx..tx+2
   if (!in_range(ty * T::SW + tx, T::SN, OOB_SHARED) ||
       !in_range((ty + 2) * T::SW + tx + 2, T::SN, OOB_SHARED))
     return;
-  float hn[9];
-  if constexpr (!ST::DEV) {
-    // FP32 storage: each lattice's pulled populations go back as two float4 and a float
-    float gn[9], fn[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      const int src = (ty + 1 - cy_of(a)) * T::SW + (tx + 1 - cx_of(a));
-      hn[a] = fmaf(hown[a], sB[src], spost[(PLANE_H + a) * T::SN + src]);
-      gn[a] = spost[(PLANE_G + a) * T::SN + src];
-      if (FLOW) fn[a] = spost[(PLANE_F + a) * T::SN + src];
-    }
-    float* __restrict__ po = static_cast<float*>(P.pout);
-    const long long nd = (long long)Y * C.rstride + X;
-    store_lattice_f32(po + PLANE_H * C.pstride, C.pstride, nd, hn);
-    store_lattice_f32(po + PLANE_G * C.pstride, C.pstride, nd, gn);
-    if (FLOW) store_lattice_f32(po + PLANE_F * C.pstride, C.pstride, nd, fn);
-    st_plane(P.phi_np1, idx, np, sum9(hn));
-  } else {
-    // 16-bit storage: the moments of the pulled populations are stored in FP32 and the
-    // moving populations as deviations from them
-    float gn[9], fn[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      const int src = (ty + 1 - cy_of(a)) * T::SW + (tx + 1 - cx_of(a));
-      hn[a] = fmaf(hown[a], sB[src], spost[(PLANE_H + a) * T::SN + src]);
-      gn[a] = spost[(PLANE_G + a) * T::SN + src];
-      if (FLOW) fn[a] = spost[(PLANE_F + a) * T::SN + src];
-    }
-    const float phin = sum9(hn);
-    st_plane(P.phi_np1, idx, np, phin);
-    typename ST::T* __restrict__ pout = static_cast<typename ST::T*>(P.pout);
-    const long long nd = (long long)Y * C.rstride + X;
-    store9<S>(pout, 0, C.pstride, nd, phin, hn);
-    const float Un = sum9(gn);
-    st_plane(P.U_np1, idx, np, Un);
-    store9<S>(pout, 1, C.pstride, nd, Un, gn);
-    if (FLOW) {
-      const float rn = sum9(fn);
-      st_plane(P.rho_np1, idx, np, rn);
-      store9<S>(pout, 2, C.pstride, nd, rn, fn);
-    }
-  }
+  pull_store<FLOW, S>(C, P, X, Y,
+                      [&](int a) { return (ty + 1 - cy_of(a)) * T::SW + (tx + 1 - cx_of(a)); },
+                      post, hown);
 }
 
 // One CTA per TX x TY tile. FP32 storage is held to 64 registers (4 CTAs of 256 threads per
-// SM, the measured optimum); the 16-bit forms keep the compiler's own allocation, which a
-// minimum-blocks bound would change.
+// SM); the 16-bit forms keep the compiler's own allocation.
 template <int TX, int TY, bool FLOW, class S, int R>
 __global__ std::enable_if_t<!Storage<S>::DEV> __launch_bounds__(TX* TY, 4)
     step_kernel(const Consts C, const StepPtrs P) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   step_tile<TX, TY, FLOW, S, R>(C, P, blockIdx.x * TX, blockIdx.y * TY, smem);
 }
 template <int TX, int TY, bool FLOW, class S, int R>
 __global__ std::enable_if_t<Storage<S>::DEV> __launch_bounds__(TX* TY)
     step_kernel(const Consts C, const StepPtrs P) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   step_tile<TX, TY, FLOW, S, R>(C, P, blockIdx.x * TX, blockIdx.y * TY, smem);
 }
 
+// ---- the column march (default scheme) ---------------------------------------------------
+// CTA of kMarchRows warps; warp w handles one row of a 32-column strip per pass. A strip of
+// grid columns [X0, X0 + 30) is collided over columns X0 - 1 .. X0 + 30 (lane l: X0 - 1 + l)
+// and pulled over lanes 1..30.
+constexpr int kMarchRows = 8;                    // rows per pass = warps per CTA
+constexpr int kMarchThreads = 32 * kMarchRows;
+constexpr int kMarchCols = 30;                   // destination columns per strip
+constexpr int kMarchPostRows = kMarchRows + 2;   // ring of collided rows
+constexpr int kMarchPhiRows = kMarchRows + 3;    // ring of phi rows
+constexpr int kMarchPW = 34;                     // phi ring row: columns X0 - 2 .. X0 + 31
+constexpr int kMarchSN = kMarchPostRows * 32;
+constexpr int kMarchPN = kMarchPhiRows * kMarchPW;
+
+template <bool FLOW>
+constexpr size_t march_smem_bytes() {
+  // collided ring, phi ring, and the pre-collision h of warp kMarchRows - 1 for two passes
+  return sizeof(float) * (PostTile::floats<FLOW>(kMarchSN) + kMarchPN + 2 * 9 * 32);
+}
+
+__host__ __device__ constexpr int march_strips(int nx) { return (nx + kMarchCols - 1) / kMarchCols; }
+
+// phi around a collided node in the phi ring: rows r0, r1, r2 (start indices of the ring rows
+// below, at and above the node) and the node's column c.
+struct RingView {
+  const float* s;
+  int r0, r1, r2, c;
+  __device__ __forceinline__ float operator()(int dx, int dy) const {
+    return s[(dy < 0 ? r0 : (dy > 0 ? r2 : r1)) + c + dx];
+  }
+  __device__ __forceinline__ bool ok() const {
+    return in_range(r0 + c - 1, kMarchPN, OOB_SHARED) && in_range(r0 + c + 1, kMarchPN, OOB_SHARED) &&
+           in_range(r1 + c - 1, kMarchPN, OOB_SHARED) && in_range(r1 + c + 1, kMarchPN, OOB_SHARED) &&
+           in_range(r2 + c - 1, kMarchPN, OOB_SHARED) && in_range(r2 + c + 1, kMarchPN, OOB_SHARED);
+  }
+};
+
+// Rows [r_begin, r_end) of the strip starting at grid column X0, by the whole CTA.
+// Pass k (k = -1 is the prologue) collides rows r0 + 1 .. r0 + 8 (r0 = r_begin + 8k; warp w
+// row r0 + 1 + w) and pulls rows r0 .. r0 + 7: warps 0..6 their own collided row, warp 7 the
+// row it collided in the pass before (its pre-collision h kept in shared memory). The pull
+// of row r reads the collided rows r - 1 .. r + 1, all in the ring of kMarchPostRows rows.
+template <bool FLOW, class S>
+__device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, int X0,
+                                            int r_begin, int r_end, float* smem) {
+  const PostTile post = PostTile::at<FLOW>(smem, kMarchSN);
+  float* sphi = smem + PostTile::floats<FLOW>(kMarchSN);
+  float* stash = sphi + kMarchPN;  // [2][9][32]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int X = X0 - 1 + lane;
+  // the strip's phi columns X0 - 2 .. X0 + 31 lie inside the grid: no ghost resolution in x
+  const bool xin = X0 >= 2 && X0 + 32 <= C.nx;
+  // ring slots, kept incrementally: the collided row of warp w in pass k is ring row
+  // (pb + w) mod kMarchPostRows of the collided ring and (qb + w) mod kMarchPhiRows of the phi
+  // ring, pb = (8k + 2) mod 10, qb = (8k + 3) mod 11 (ring row 0: row r_begin - 1, resp. - 2)
+  const auto wrapP = [](int v) { return v < 0 ? v + kMarchPostRows : (v >= kMarchPostRows ? v - kMarchPostRows : v); };
+  const auto wrapQ = [](int v) { return v < 0 ? v + kMarchPhiRows : (v >= kMarchPhiRows ? v - kMarchPhiRows : v); };
+  int pb = (2 - kMarchRows + 2 * kMarchPostRows) % kMarchPostRows;
+  int qb = (3 - kMarchRows + 2 * kMarchPhiRows) % kMarchPhiRows;
+  for (int k = -1;; ++k) {
+    const int r0 = r_begin + kMarchRows * k;
+    const int rc = r0 + 1 + w;  // collision row of this warp
+    const bool collide = (k >= 0 || w >= kMarchRows - 2) && rc <= r_end && rc <= C.ny &&
+                         X <= C.nx;
+    const int sc = wrapP(pb + w);  // collided-ring row of rc
+    const int qc = wrapQ(qb + w);  // phi-ring row of rc
+
+    // ---- A: the new phi rows of this pass (the prologue: the four below the first) ----
+    {
+      const int rl = r0 + 2 + w;
+      if ((k >= 0 || w >= kMarchRows - 4) && rl <= r_end + 1 && rl <= C.ny + 1) {
+        float* row = sphi + wrapQ(qc + 1) * kMarchPW;
+        const bool yin = rl >= 0 && rl < C.ny;
+        for (int c = lane; c < kMarchPW; c += 32) {
+          const int xg = X0 - 2 + c;
+          float v;
+          if (xin && yin) {
+            v = ldg_plane(P.phi_n, (long long)rl * C.pitch + xg, (long long)C.pitch * C.ny);
+          } else {
+            int gx, gy;
+            v = -1.0f;
+            if (xg > C.nx + 1) {
+              v = 0.0f;  // beyond the grid's halo (ragged last strip): never read
+            } else if (axis_phi(xg, C.nx, C.bc[0], C.bc[1], gx) &&
+                       axis_phi(rl, C.ny, C.bc[2], C.bc[3], gy)) {
+              v = ldg_plane(P.phi_n, (long long)gy * C.pitch + gx, (long long)C.pitch * C.ny);
+            }
+          }
+          if (in_range(row - sphi + c, kMarchPN, OOB_SHARED)) row[c] = v;
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- B: collide row rc ----
+    float hown[9];
+    if (collide) {
+      const auto view_at = [&](int shx, int shy) {
+        const int q = wrapQ(qc + shy);  // phi ring row of the mapped row
+        return RingView{sphi, wrapQ(q - 1) * kMarchPW, q * kMarchPW, wrapQ(q + 1) * kMarchPW,
+                        lane + 1 + shx};
+      };
+      collide_source<FLOW, S, true, 1>(C, P, X, rc, sc * 32 + lane, view_at, post, hown);
+      if (w == kMarchRows - 1) {
+        float* st = stash + (k & 1) * 9 * 32;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) st[a * 32 + lane] = hown[a];
+      }
+    }
+    __syncthreads();
+
+    // ---- C: pull row rp ----
+    if (k >= 0) {
+      const int rp = w < kMarchRows - 1 ? rc : r0;
+      if (rp < r_end && rp < C.ny && lane >= 1 && lane <= kMarchCols && X < C.nx) {
+        if (w == kMarchRows - 1) {
+          const float* st = stash + ((k - 1) & 1) * 9 * 32;
+#pragma unroll
+          for (int a = 0; a < 9; ++a) hown[a] = st[a * 32 + lane];
+        }
+        // collided-ring row of rp: sc (warps 0..6), or that of r0 (warp 7)
+        const int sp = w < kMarchRows - 1 ? sc : wrapP(pb - 1);
+        const int s_m = wrapP(sp - 1) * 32 + lane;
+        const int s_0 = sp * 32 + lane;
+        const int s_p = wrapP(sp + 1) * 32 + lane;
+        if (in_range(s_m - 1, kMarchSN, OOB_SHARED) && in_range(s_0 + 1, kMarchSN, OOB_SHARED) &&
+            in_range(s_p + 1, kMarchSN, OOB_SHARED))
+          pull_store<FLOW, S>(C, P, X, rp,
+                              [&](int a) {
+                                const int cy = cy_of(a);
+                                return (cy > 0 ? s_m : (cy < 0 ? s_p : s_0)) - cx_of(a);
+                              },
+                              post, hown);
+      }
+    }
+    pb = wrapP(pb + kMarchRows);
+    qb = wrapQ(qb + kMarchRows);
+    if (r0 + kMarchRows >= r_end) break;  // rows r_begin .. r0 + 7 are done
+  }
+}
+
+// Rows of the strip segment a march CTA walks: tall enough that the two extra rows collided
+// where a segment starts cost little, short enough that a launch has many CTAs. CTAs are
+// numbered strip-fastest, so the CTAs resident at one time cover whole bands of rows, and
+// neighbouring strips (which re-read each other's edge columns) run side by side.
+__host__ __device__ constexpr int march_seg_rows(int ny) {
+  return ny < 64 ? ((ny + kMarchRows - 1) / kMarchRows) * kMarchRows : 64;
+}
+
+// One CTA per (strip, segment): blockIdx.x the strip, blockIdx.y the segment. Held to 64
+// registers (4 CTAs of 256 threads per SM).
+template <bool FLOW, class S>
+__global__ std::enable_if_t<!Storage<S>::DEV> __launch_bounds__(kMarchThreads, 4)
+    march_kernel(const Consts C, const StepPtrs P) {
+  extern __shared__ __align__(16) float smem[];
+  const int H = march_seg_rows(C.ny), r0 = blockIdx.y * H;
+  march_range<FLOW, S>(C, P, blockIdx.x * kMarchCols, r0, min(C.ny, r0 + H), smem);
+}
+template <bool FLOW, class S>
+__global__ std::enable_if_t<Storage<S>::DEV> __launch_bounds__(kMarchThreads, 4)
+    march_kernel(const Consts C, const StepPtrs P) {
+  extern __shared__ __align__(16) float smem[];
+  const int H = march_seg_rows(C.ny), r0 = blockIdx.y * H;
+  march_range<FLOW, S>(C, P, blockIdx.x * kMarchCols, r0, min(C.ny, r0 + H), smem);
+}
+
 // ---- many grids in one launch ----------------------------------------------------------
-// Tile shapes of 256 threads that the batched kernel can use for a member grid; the
-// autotuner picks one per grid size. Each shape is its own kernel instantiation, launched
-// with exactly its shared memory (a larger request shrinks the L1 left for the pull).
-constexpr int kNumShapes = 3;
-__host__ __device__ constexpr int shape_tx(int s) { return s == 0 ? 32 : s == 1 ? 64 : 16; }
-__host__ __device__ constexpr int shape_ty(int s) { return s == 0 ? 8 : s == 1 ? 4 : 16; }
+// Shapes a member grid of a batched launch can use; the autotuner picks one per grid size.
+// Shape 0 is the column march (one persistent wave over all its members); 1..3 are 2D tiles
+// of 256 threads, each its own kernel instantiation launched with exactly its shared memory.
+constexpr int kNumShapes = 4;
+__host__ __device__ constexpr int shape_tx(int s) { return s == 1 ? 32 : s == 2 ? 64 : 16; }
+__host__ __device__ constexpr int shape_ty(int s) { return s == 1 ? 8 : s == 2 ? 4 : 16; }
 
 // One member grid of a batched launch: its constants, the buffer roles of this step and its
-// tile count per row in the launch's shape.
+// tile count per row in the launch's shape (march: its strip count).
 struct BatchDesc {
   Consts C;
   StepPtrs P;
@@ -558,36 +795,56 @@ struct BatchDesc {
 };
 
 // Parameter block of one batched launch: up to kBatchMaxMembers grids, list position k owning
-// tiles tile_start[k] .. tile_start[k+1]-1 (row-major within the grid). It travels as a
-// __grid_constant__ kernel parameter, so the descriptors sit in the constant bank (no device
-// buffer to upload, nothing to race with launches still queued) and the block stays within
-// the 32,764-byte parameter limit.
+// work units start[k] .. start[k+1]-1 (tiles, row-major within the grid; march: (strip, row)
+// pairs, strip-major). It travels as a __grid_constant__ kernel parameter, so the descriptors
+// sit in the constant bank (no device buffer to upload, nothing to race with launches still
+// queued) and the block stays within the 32,764-byte parameter limit.
 constexpr int kBatchMaxMembers = LBMICE_BATCH_MAX_PER_LAUNCH;
 struct BatchLaunch {
   int n;
-  int tile_start[kBatchMaxMembers + 1];
+  long long tile_start[kBatchMaxMembers + 1];
   BatchDesc d[kBatchMaxMembers];
 };
 static_assert(sizeof(BatchLaunch) <= 32764, "kernel parameter limit");
 
-// One CTA per tile of a batched launch: binary search for the owning grid, then the
-// single-grid tile code. A tile beyond its grid (a malformed block) is skipped.
-template <int TX, int TY, bool FLOW, class S>
-__global__ void __launch_bounds__(TX* TY, 4) batch_step_kernel(const __grid_constant__ BatchLaunch L) {
-  extern __shared__ float smem[];
-  const int t = blockIdx.x;
-  int lo = 0, hi = L.n - 1;  // last list position whose first tile is <= t
+// Last list position whose first unit is <= t.
+__device__ __forceinline__ int batch_member_of(const BatchLaunch& L, long long t) {
+  int lo = 0, hi = L.n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (L.tile_start[mid] <= t) lo = mid; else hi = mid - 1;
   }
-  const BatchDesc& d = L.d[lo];
-  const int local = t - L.tile_start[lo];
+  return lo;
+}
+
+// One CTA per tile of a batched launch: the owning grid, then the single-grid tile code. A
+// tile beyond its grid (a malformed block) is skipped.
+template <int TX, int TY, bool FLOW, class S>
+__global__ void __launch_bounds__(TX* TY, 4) batch_step_kernel(const __grid_constant__ BatchLaunch L) {
+  extern __shared__ __align__(16) float smem[];
+  const long long t = blockIdx.x;
+  const int m = batch_member_of(L, t);
+  const BatchDesc& d = L.d[m];
+  const int local = (int)(t - L.tile_start[m]);
   const int tyi = local / d.tiles_x, txi = local - tyi * d.tiles_x;
   if (local < 0 || tyi * TY >= d.C.ny) return;
   // no own-node preload here: the batched tile is more issue-bound than the single-grid one
-  // and measured 2.7% faster without it
   step_tile<TX, TY, FLOW, S, 1, false>(d.C, d.P, txi * TX, tyi * TY, smem);
+}
+
+// One CTA per (strip, segment) of the members of a march launch, numbered member by member,
+// strip-fastest within a member.
+template <bool FLOW, class S>
+__global__ void __launch_bounds__(kMarchThreads, 4) batch_march_kernel(const __grid_constant__ BatchLaunch L) {
+  extern __shared__ __align__(16) float smem[];
+  const long long t = blockIdx.x;
+  const int m = batch_member_of(L, t);
+  const BatchDesc& d = L.d[m];
+  const int local = (int)(t - L.tile_start[m]);
+  const int seg = local / d.tiles_x, strip = local - seg * d.tiles_x;
+  const int H = march_seg_rows(d.C.ny), r0 = seg * H;
+  if (local < 0 || r0 >= d.C.ny) return;
+  march_range<FLOW, S>(d.C, d.P, strip * kMarchCols, r0, min(d.C.ny, r0 + H), smem);
 }
 
 }  // namespace lbmice

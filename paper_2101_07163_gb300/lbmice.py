@@ -277,7 +277,7 @@ class Lattice:
         return dict(zip(STAT_NAMES, list(out)))
 
 
-SHAPES = {0: (32, 8), 1: (64, 4), 2: (16, 16)}
+SHAPES = {0: "march", 1: "32x8", 2: "64x4", 3: "16x16"}  # LBMICE_SHAPE_*
 BATCH_MAX_PER_LAUNCH = 128  # members one batched launch carries (LBMICE_BATCH_MAX_PER_LAUNCH)
 
 
@@ -302,7 +302,7 @@ class _Member(Lattice):
 
 
 class Batch:
-    """Many grids advanced together, one kernel launch per step for each tile shape in use
+    """Many grids advanced together, one kernel launch per step for each shape in use
     (include/lbmice.h, lbmice_batch_*). ``configs``: a list of keyword dicts, each with nx, ny
     and the make_params keywords of one member; all share flow and storage."""
 
@@ -350,7 +350,7 @@ class Batch:
         _check(lib().lbmice_batch_step(self._h, int(n)), "lbmice_batch_step")
 
     def autotune(self, steps_per_trial: int = 6):
-        """Pick a tile shape per grid size; returns (shapes, steps_taken)."""
+        """Pick a shape per grid size; returns (shapes, steps_taken)."""
         n = len(self.members)
         shapes = (ctypes.c_int32 * n)()
         taken = ctypes.c_int64()
@@ -365,7 +365,7 @@ class Batch:
 
     @property
     def launches_per_step(self) -> int:
-        """Kernel launches of one batched step: per tile shape in use, one per
+        """Kernel launches of one batched step: per shape in use, one per
         BATCH_MAX_PER_LAUNCH members of that shape."""
         return sum(-(-self.shapes.count(s) // BATCH_MAX_PER_LAUNCH) for s in SHAPES)
 

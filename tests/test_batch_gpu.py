@@ -1,7 +1,8 @@
 """Batched launch: many grids of uneven sizes, parameters and faces in one persistent kernel
-per step. Every node is computed by the same tile code as the single-grid kernel, whatever the
-tile shape (with its arithmetic rounding written out, so no kernel contracts it differently),
-so a batch must reproduce independently stepped single grids bit for bit."""
+per step. Every node is collided by the same code as in the single-grid kernel, whatever the
+shape (the column march or a 2D tile; its arithmetic rounding written out, so no kernel
+contracts it differently), so a batch must reproduce independently stepped single grids bit
+for bit."""
 import ctypes
 
 import numpy as np
@@ -37,7 +38,7 @@ def test_batch_equals_single_grids_for_every_tile_shape(storage):
     b = lbmice.Batch(configs(ws, storage))
     for i, (m, w) in enumerate(zip(b.members, ws)):
         m.init_seed(w.cx, w.cy, w.R0, w.U0)
-        b.set_shape(i, i % 3)  # all three shapes in one launch
+        b.set_shape(i, i % 4)  # all four shapes in one step
     ref = singles(ws, storage)
     b.step(125)  # two graph replays of 60 steps and five single launches
     for lat in ref:
@@ -54,8 +55,8 @@ def test_autotune_keeps_members_in_lockstep():
         m.init_seed(w.cx, w.cy, w.R0, w.U0)
     shapes, taken = b.autotune(steps_per_trial=2)
     classes = len({w.nx for w in ws})
-    assert taken == classes * 3 * 3
-    assert set(shapes) <= {0, 1, 2}
+    assert taken == classes * 4 * 3
+    assert set(shapes) <= {0, 1, 2, 3}
     # results do not depend on the shapes the autotuner tried
     ref = singles(ws)
     for lat in ref:
@@ -125,7 +126,7 @@ def test_batch_members_against_the_oracle():
     for i, (m, w) in enumerate(zip(b.members, ws)):
         f = W.perturbed_fields(w, 30 + i)
         m.set_fields(**f)
-        b.set_shape(i, (i + 1) % 3)
+        b.set_shape(i, (i + 1) % 4)
         o = oracle.Oracle(nx=w.nx, ny=w.ny, **w.params())
         o.set_fields(**f)
         orcs.append(o)

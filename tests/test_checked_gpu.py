@@ -2,7 +2,7 @@
 and shared-memory index of the single-grid and batched step kernels is tested against its
 buffer before the access, a violation sets a bit of a device word and skips the access.
 Nothing traps. It runs in a child process with LBMICE_CHECKED=1, on small and ragged grids
-with every face rule, storage and stencil, and on a batch with all three tile shapes: no
+with every face rule, storage and stencil, and on a batch with all four shapes: no
 index may leave its buffer. The checks themselves are exercised by shrinking the extents
 they use (lbmice_debug_set_margin), so that accesses near the end of a buffer, still inside
 it, are reported and skipped."""
@@ -51,7 +51,7 @@ ws = W.batch_sweep(count=6, seed=11, sides=(40, 72, 100))
 b = lbmice.Batch([dict(nx=w.nx, ny=w.ny, **w.params()) for w in ws])
 for i, (m, w) in enumerate(zip(b.members, ws)):
     m.init_seed(w.cx, w.cy, w.R0, w.U0)
-    b.set_shape(i, i % 3)
+    b.set_shape(i, i % 4)
 b.step(61)
 b.close()
 res["runs"] = runs + 1
