@@ -1,5 +1,7 @@
 // C ABI of the coupled lattice-Boltzmann ice-crystal step (include/lbmice.h): parameter
 // derivation, device state, kernel launches and CUDA-graph replay of step chunks.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +31,8 @@ constexpr int kTX = 32, kTY = 8; // destination tile of the step kernel
 // the phi triple buffer (period 3) are back in their slots after each replay.
 constexpr int kGraphSteps = 60;
 constexpr int kStatBlocks = 608; // 4 x 152 SMs
+constexpr int kPhases = 6;       // buffer rotation period: populations 2, phi planes 3
+constexpr int kMapsPerPhase = 5; // tensor maps of one step's inputs (StepPtrs::tm)
 
 }  // namespace
 
@@ -51,6 +55,9 @@ struct lbmice_ctx {
   double* stat_host = nullptr;     // pinned
   cudaGraphExec_t graph = nullptr;
   int64_t step = 0;
+  // tensor maps of the march's L2 prefetch, kMapsPerPhase per step phase (step mod 6), in
+  // device memory
+  CUtensorMap* tmaps = nullptr;
 };
 
 namespace {
@@ -142,6 +149,7 @@ void release(lbmice_t* h) {
   if (h->stat_partial) cudaFree(h->stat_partial);
   if (h->stat_out) cudaFree(h->stat_out);
   if (h->stat_host) cudaFreeHost(h->stat_host);
+  if (h->tmaps) cudaFree(h->tmaps);
   if (h->capture) cudaStreamDestroy(h->capture);
   delete h;
 }
@@ -155,6 +163,84 @@ size_t field_bytes(const lbmice_t* h) {
   return sizeof(float) * (size_t)h->C.pitch * (size_t)h->C.ny;
 }
 bool dev16(const lbmice_t* h) { return h->p.storage != LBMICE_STORAGE_F32; }
+
+// cuTensorMapEncodeTiled of the driver, through the runtime's entry-point query (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// A tiled tensor map of rank 2 or 3 over base: dims[0] the contiguous extent (elements),
+// strides[i] the bytes between steps of dimension i + 1, box the box extents.
+bool encode_map(CUtensorMap* m, CUtensorMapDataType t, int rank, const void* base,
+                const uint64_t* dims, const uint64_t* strides, const uint32_t* box) {
+  auto fn = encode_tiled();
+  if (!fn) return false;
+  cuuint64_t d[3], st[2];
+  cuuint32_t b[3], es[3] = {1, 1, 1};
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+  }
+  for (int i = 0; i + 1 < rank; ++i) st[i] = strides[i];
+  return fn(m, t, (cuuint32_t)rank, const_cast<void*>(base), d, st, b, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// The maps of every step phase (the boxes of one march pass: 8 rows of a strip), encoded on
+// the host and copied to the device once; the buffers never move.
+int make_tensor_maps(lbmice_t* h) {
+  std::vector<CUtensorMap> maps(kPhases * kMapsPerPhase);
+  std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+  const uint64_t P = h->C.pitch, NY = h->C.ny, Q = h->C.pstride;
+  const uint32_t R = kMarchRows;
+  bool ok = true;
+  for (int ph = 0; ph < kPhases && ok; ++ph) {
+    CUtensorMap* m = &maps[ph * kMapsPerPhase];
+    const char* pin = static_cast<const char*>(h->pops[ph & 1]);
+    const uint64_t d1[2] = {P, NY}, s1[1] = {P * 4};
+    const uint32_t b1[2] = {36, R};
+    if (!dev16(h)) {
+      const uint64_t dq[3] = {4 * P, NY, 4}, sq[2] = {16 * P, 16 * Q};
+      const uint32_t bq[3] = {128, R, 4};
+      ok = ok && encode_map(&m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, pin, dq, sq, bq);
+      const uint64_t d0[2] = {2 * P, NY}, s0[1] = {8 * P};
+      const uint32_t b0[2] = {68, R};
+      ok = ok && encode_map(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pin + 64 * Q, d0, s0, b0);
+      if (h->p.flow) {
+        const uint64_t df[3] = {4 * P, NY, 2};
+        const uint32_t bf[3] = {128, R, 2};
+        ok = ok && encode_map(&m[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, pin + 72 * Q, df, sq, bf);
+        ok = ok && encode_map(&m[3], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pin + 104 * Q, d1, s1, b1);
+      }
+    } else {
+      const uint32_t L = h->p.flow ? 3 : 2;
+      const uint64_t dv[3] = {8 * P, NY, L}, sv[2] = {16 * P, 18 * Q};
+      const uint32_t bv[3] = {256, R, L};
+      ok = ok && encode_map(&m[0], CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, pin, dv, sv, bv);
+      ok = ok && encode_map(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->Um[ph & 1], d1, s1, b1);
+      if (h->p.flow)
+        ok = ok && encode_map(&m[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->rhom[ph & 1], d1, s1, b1);
+    }
+    ok = ok && encode_map(&m[4], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->phi[(ph + 2) % 3], d1, s1, b1);
+  }
+  if (!ok) return LBMICE_ECUDA;
+  LB_TRY(cudaMalloc(&h->tmaps, sizeof(CUtensorMap) * maps.size()));
+  LB_TRY(cudaMemcpy(h->tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                    cudaMemcpyHostToDevice));
+  return LBMICE_OK;
+}
 
 // Run f with a tag value of the handle's storage type.
 template <class Fn>
@@ -176,17 +262,44 @@ long long march_units(const Consts& C) {
   return (long long)march_strips(C.nx) * ((C.ny + H - 1) / H);
 }
 
+// Opt the march kernels of this storage into the shared memory they use (above 48 KB).
+int march_attributes(const lbmice_t* h) {
+  return with_storage(h, [&](auto tag) -> int {
+    using S = decltype(tag);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](auto kern, size_t bytes) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    set(march_kernel<true, S, MARCH_PREFETCH>, march_smem_bytes<true>());
+    set(march_kernel<false, S, MARCH_PREFETCH>, march_smem_bytes<false>());
+    set(march_kernel<true, S, MARCH_PLAIN>, march_smem_bytes<true>());
+    set(march_kernel<false, S, MARCH_PLAIN>, march_smem_bytes<false>());
+    set(batch_march_kernel<true, S, MARCH_PREFETCH>, march_smem_bytes<true>());
+    set(batch_march_kernel<false, S, MARCH_PREFETCH>, march_smem_bytes<false>());
+    return cuda_err(e);
+  });
+}
+
 // One step of grid h on the given buffers.
 int launch_step_ptrs(const lbmice_t* h, const StepPtrs& P, cudaStream_t st) {
   if (h->C.stencil == 4 && h->C.fold == 6) {
-    // the default scheme (E4, six-fold): the column march
+    // the default scheme (E4, six-fold): the column march, its populations prefetched into
+    // L2 by TMA when the step's buffers have tensor maps
     const dim3 grid = march_grid(h->C);
     return with_storage(h, [&](auto tag) {
       using S = decltype(tag);
-      if (h->p.flow)
-        march_kernel<true, S><<<grid, kMarchThreads, march_smem_bytes<true>(), st>>>(h->C, P);
-      else
-        march_kernel<false, S><<<grid, kMarchThreads, march_smem_bytes<false>(), st>>>(h->C, P);
+      auto go = [&](auto flow, auto pref) {
+        constexpr bool F = decltype(flow)::value;
+        constexpr int M = decltype(pref)::value ? MARCH_PREFETCH : MARCH_PLAIN;
+        march_kernel<F, S, M><<<grid, kMarchThreads, march_smem_bytes<F>(), st>>>(h->C, P);
+      };
+      const bool pref = P.tm != nullptr;
+      if (h->p.flow) {
+        if (pref) go(std::true_type{}, std::true_type{}); else go(std::true_type{}, std::false_type{});
+      } else {
+        if (pref) go(std::false_type{}, std::true_type{}); else go(std::false_type{}, std::false_type{});
+      }
       return cuda_err(cudaGetLastError());
     });
   }
@@ -217,6 +330,7 @@ int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
   P.U_np1 = h->Um[(s + 1) & 1];
   P.rho_n = h->rhom[s & 1];
   P.rho_np1 = h->rhom[(s + 1) & 1];
+  P.tm = h->tmaps + kMapsPerPhase * (s % kPhases);
   return launch_step_ptrs(h, P, st);
 }
 
@@ -342,6 +456,13 @@ int lbmice_create(const lbmice_params* p, void* stream, lbmice_t** out) {
     release(h);
     cudaGetLastError();  // clear a sticky-free error state left by a failed allocation
     return cuda_err(e);
+  }
+  rc = march_attributes(h);
+  if (rc == LBMICE_OK) rc = make_tensor_maps(h);
+  if (rc != LBMICE_OK) {
+    release(h);
+    cudaGetLastError();
+    return rc;
   }
   *out = h;
   return LBMICE_OK;
@@ -760,6 +881,7 @@ StepPtrs step_ptrs(const lbmice_t* h, int ph) {
   P.U_np1 = h->Um[(ph + 1) & 1];
   P.rho_n = h->rhom[ph & 1];
   P.rho_np1 = h->rhom[(ph + 1) & 1];
+  P.tm = h->tmaps + kMapsPerPhase * ph;
   return P;
 }
 
@@ -781,10 +903,10 @@ int launch_march_block(const lbmice_batch_t* b, long long units, cudaStream_t st
   return with_storage(b->members[0], [&](auto tag) {
     using S = decltype(tag);
     if (b->flow)
-      batch_march_kernel<true, S>
+      batch_march_kernel<true, S, MARCH_PREFETCH>
           <<<(unsigned)units, kMarchThreads, march_smem_bytes<true>(), st>>>(*b->block);
     else
-      batch_march_kernel<false, S>
+      batch_march_kernel<false, S, MARCH_PREFETCH>
           <<<(unsigned)units, kMarchThreads, march_smem_bytes<false>(), st>>>(*b->block);
     return cuda_err(cudaGetLastError());
   });

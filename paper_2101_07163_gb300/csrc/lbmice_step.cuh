@@ -26,6 +26,7 @@
 
 #include "../../include/lbmice.h"
 #include "lbmice_device.cuh"
+#include "lbmice_tma.cuh"
 
 namespace lbmice {
 
@@ -39,6 +40,10 @@ struct StepPtrs {
   float* __restrict__ U_np1;
   const float* __restrict__ rho_n;
   float* __restrict__ rho_np1;
+  // tensor maps of this step's inputs (in device memory) for the march's L2 prefetch:
+  // FP32 (h,g) quads, (h_0,g_0) pairs, f quads, f_0, phi^{n-1}; 16-bit: the deviation
+  // vectors, U^n, rho^n, (unused), phi^{n-1}. Null: no prefetch.
+  const CUtensorMap* tm;
 };
 
 // Collided populations of SN source nodes in shared memory: (h*_a / a_s^2, g*_a) pairs,
@@ -132,6 +137,34 @@ __device__ __forceinline__ void own_load(const Consts& C, const StepPtrs& P, int
     }
   }
   in.php = ldg_plane(P.phi_nm1, idx, np);
+}
+
+// ---- L2 prefetch of a march pass -----------------------------------------------------------
+// The populations a march pass collides (rows y .. y + 7, columns X0 - 1 .. X0 + 30) are
+// prefetched into L2 by TMA a pass ahead, one box per stored plane group, so that the pass's
+// own loads after the phi barrier hit L2: FP32 (h,g) quads [4][8][32 x 4 floats], (h_0,g_0)
+// pairs [8][34 from column X0 - 2], f quads [2][8][32 x 4], f_0 and phi^{n-1} [8][36 from
+// column xa]; 16-bit deviation vectors [3][8][32 x 8 halves], U, rho and phi^{n-1} [8][36],
+// with xa = (X0 - 1) rounded down to a multiple of 4, so that every box starts on a 16-byte
+// boundary (parts outside the grid are skipped). Tensor map slots (StepPtrs::tm): FP32 quads,
+// pairs, f quads, f_0, phi^{n-1}; 16-bit vectors, U, rho, (unused), phi^{n-1}.
+// Thread 0: prefetch into L2 the boxes of the pass whose collided rows start at row y.
+template <bool FLOW, class S>
+__device__ __forceinline__ void prefetch_issue(const StepPtrs& P, int X0, int y) {
+  const int xa = (X0 - 1) & ~3;
+  if constexpr (!Storage<S>::DEV) {
+    tma_prefetch_3d(P.tm + 0, 4 * (X0 - 1), y, 0);
+    tma_prefetch_2d(P.tm + 1, 2 * (X0 - 2), y);
+    if (FLOW) {
+      tma_prefetch_3d(P.tm + 2, 4 * (X0 - 1), y, 0);
+      tma_prefetch_2d(P.tm + 3, xa, y);
+    }
+  } else {
+    tma_prefetch_3d(P.tm + 0, 8 * (X0 - 1), y, 0);
+    tma_prefetch_2d(P.tm + 1, xa, y);
+    if (FLOW) tma_prefetch_2d(P.tm + 2, xa, y);
+  }
+  tma_prefetch_2d(P.tm + 4, xa, y);
 }
 
 // Deviations (d^h_a, d^g_a) of a node from its two 16-bit vectors; the rest pair is minus the
@@ -625,9 +658,16 @@ constexpr int kMarchPW = 34;                     // phi ring row: columns X0 - 2
 constexpr int kMarchSN = kMarchPostRows * 32;
 constexpr int kMarchPN = kMarchPhiRows * kMarchPW;
 
+// Own-population loads of the march: plain loads after the phi barrier, or the same loads of
+// boxes a TMA prefetch brought into L2 kMarchAhead passes ahead (when the step's buffers have
+// tensor maps).
+enum : int { MARCH_PLAIN = 0, MARCH_PREFETCH = 1 };
+constexpr int kMarchAhead = 1;
+
+// Shared memory of a march CTA: the collided ring, the phi ring and the pre-collision h of
+// warp kMarchRows - 1 for two passes.
 template <bool FLOW>
-constexpr size_t march_smem_bytes() {
-  // collided ring, phi ring, and the pre-collision h of warp kMarchRows - 1 for two passes
+__host__ __device__ constexpr size_t march_smem_bytes() {
   return sizeof(float) * (PostTile::floats<FLOW>(kMarchSN) + kMarchPN + 2 * 9 * 32);
 }
 
@@ -653,15 +693,19 @@ struct RingView {
 // row r0 + 1 + w) and pulls rows r0 .. r0 + 7: warps 0..6 their own collided row, warp 7 the
 // row it collided in the pass before (its pre-collision h kept in shared memory). The pull
 // of row r reads the collided rows r - 1 .. r + 1, all in the ring of kMarchPostRows rows.
-template <bool FLOW, class S>
+// PREF: thread 0 prefetches the boxes of pass k + kMarchAhead into L2 as pass k starts.
+template <bool FLOW, class S, int MODE>
 __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, int X0,
                                             int r_begin, int r_end, float* smem) {
+  constexpr bool PREF = MODE == MARCH_PREFETCH;
   const PostTile post = PostTile::at<FLOW>(smem, kMarchSN);
   float* sphi = smem + PostTile::floats<FLOW>(kMarchSN);
   float* stash = sphi + kMarchPN;  // [2][9][32]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int X = X0 - 1 + lane;
-  // the strip's phi columns X0 - 2 .. X0 + 31 lie inside the grid: no ghost resolution in x
+  if (PREF && threadIdx.x == 0)
+    for (int j = 0; j < kMarchAhead && r_begin + kMarchRows * j < r_end; ++j)
+      prefetch_issue<FLOW, S>(P, X0, r_begin + kMarchRows * j + 1);
   const bool xin = X0 >= 2 && X0 + 32 <= C.nx;
   // ring slots, kept incrementally: the collided row of warp w in pass k is ring row
   // (pb + w) mod kMarchPostRows of the collided ring and (qb + w) mod kMarchPhiRows of the phi
@@ -677,6 +721,8 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
                          X <= C.nx;
     const int sc = wrapP(pb + w);  // collided-ring row of rc
     const int qc = wrapQ(qb + w);  // phi-ring row of rc
+    if (PREF && threadIdx.x == 0 && k >= 0 && r0 + kMarchRows * kMarchAhead < r_end)
+      prefetch_issue<FLOW, S>(P, X0, r0 + kMarchRows * kMarchAhead + 1);
 
     // ---- A: the new phi rows of this pass (the prologue: the four below the first) ----
     {
@@ -762,19 +808,11 @@ __host__ __device__ constexpr int march_seg_rows(int ny) {
 
 // One CTA per (strip, segment): blockIdx.x the strip, blockIdx.y the segment. Held to 64
 // registers (4 CTAs of 256 threads per SM).
-template <bool FLOW, class S>
-__global__ std::enable_if_t<!Storage<S>::DEV> __launch_bounds__(kMarchThreads, 4)
-    march_kernel(const Consts C, const StepPtrs P) {
-  extern __shared__ __align__(16) float smem[];
+template <bool FLOW, class S, int MODE>
+__global__ void __launch_bounds__(kMarchThreads, 4) march_kernel(const Consts C, const StepPtrs P) {
+  extern __shared__ __align__(16) float march_smem[];
   const int H = march_seg_rows(C.ny), r0 = blockIdx.y * H;
-  march_range<FLOW, S>(C, P, blockIdx.x * kMarchCols, r0, min(C.ny, r0 + H), smem);
-}
-template <bool FLOW, class S>
-__global__ std::enable_if_t<Storage<S>::DEV> __launch_bounds__(kMarchThreads, 4)
-    march_kernel(const Consts C, const StepPtrs P) {
-  extern __shared__ __align__(16) float smem[];
-  const int H = march_seg_rows(C.ny), r0 = blockIdx.y * H;
-  march_range<FLOW, S>(C, P, blockIdx.x * kMarchCols, r0, min(C.ny, r0 + H), smem);
+  march_range<FLOW, S, MODE>(C, P, blockIdx.x * kMarchCols, r0, min(C.ny, r0 + H), march_smem);
 }
 
 // ---- many grids in one launch ----------------------------------------------------------
@@ -833,10 +871,10 @@ __global__ void __launch_bounds__(TX* TY, 4) batch_step_kernel(const __grid_cons
 }
 
 // One CTA per (strip, segment) of the members of a march launch, numbered member by member,
-// strip-fastest within a member.
-template <bool FLOW, class S>
+// strip-fastest within a member; the members' populations are prefetched as in march_kernel.
+template <bool FLOW, class S, int MODE>
 __global__ void __launch_bounds__(kMarchThreads, 4) batch_march_kernel(const __grid_constant__ BatchLaunch L) {
-  extern __shared__ __align__(16) float smem[];
+  extern __shared__ __align__(16) float march_smem[];
   const long long t = blockIdx.x;
   const int m = batch_member_of(L, t);
   const BatchDesc& d = L.d[m];
@@ -844,7 +882,7 @@ __global__ void __launch_bounds__(kMarchThreads, 4) batch_march_kernel(const __g
   const int seg = local / d.tiles_x, strip = local - seg * d.tiles_x;
   const int H = march_seg_rows(d.C.ny), r0 = seg * H;
   if (local < 0 || r0 >= d.C.ny) return;
-  march_range<FLOW, S>(d.C, d.P, strip * kMarchCols, r0, min(d.C.ny, r0 + H), smem);
+  march_range<FLOW, S, MODE>(d.C, d.P, strip * kMarchCols, r0, min(d.C.ny, r0 + H), march_smem);
 }
 
 }  // namespace lbmice
