@@ -39,6 +39,7 @@ ALGO_BYTES_PER_LUP = {("f32", 3): 224, ("f32", 2): 152, ("f16", 3): 116, ("f16",
 DESIGN_BYTES_PER_LUP = {("f32", 3): 228, ("f32", 2): 156, ("f16", 3): 124, ("f16", 2): 84,
                         ("bf16", 3): 124, ("bf16", 2): 84}
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal (the measured copy peak is the denominator)
 
 
 def parse():
@@ -51,7 +52,7 @@ def parse():
     ap.add_argument("--nx", type=int, default=0, help="override grid (profiling runs)")
     ap.add_argument("--ny", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--storage-legs", default="f16,bf16",
                     help="16-bit storage legs timed after the FP32 leg ('' for none)")
     ap.add_argument("--batch-steps", type=int, default=120,
@@ -217,14 +218,25 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def oracle_run(w: W.Workload, fields: dict, seconds: float, min_steps: int = 2):
-    """Time the FP64 oracle on this workload, one full-grid step at a time."""
+def host_cores() -> int:
+    """Host threads the oracle may use: the CPUs this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_run(w: W.Workload, fields: dict, seconds: float, min_steps: int = 2,
+               threads: int = 1, max_steps: int = 64):
+    """Time the FP64 oracle on this workload, one full-grid step at a time, on `threads`
+    host threads (its rows split statically; same bits for any count)."""
     import oracle
+    oracle.set_threads(threads)
     o = oracle.Oracle(nx=w.nx, ny=w.ny, **w.params())
     o.set_fields(**fields)
     t0 = time.perf_counter()
     n = 0
-    while n < min_steps or (time.perf_counter() - t0 < seconds and n < 64):
+    while n < min_steps or (time.perf_counter() - t0 < seconds and n < max_steps):
         o.step(1)
         n += 1
     dt = time.perf_counter() - t0
@@ -238,10 +250,20 @@ def run_reference(args):
     import oracle
     w = workload(args)
     full = W.seed_fields(w)
-    # one bench step = one oracle step on a band of rows through the crystal, sized so that
-    # warmup + steps take about two minutes on one host core at ~3.5 MLUPS
+    cores = host_cores()
+    oracle.set_threads(cores)
+    # one bench step = one oracle step on a band of rows through the crystal, sized from a
+    # one-step probe so that warmup + steps take about two minutes on all host cores
     total = max(1, args.steps + args.warmup)
-    rows = int(np.clip(round(120.0 * 3.5e6 / (w.nx * total)), 4, w.ny))
+    probe_rows = min(w.ny, 64)
+    pf = {k: np.ascontiguousarray(v[:probe_rows]) for k, v in full.items()}
+    po = oracle.Oracle(nx=w.nx, ny=probe_rows, **W.Workload(**{**w.__dict__, "ny": probe_rows}).params())
+    po.set_fields(**pf)
+    t0 = time.perf_counter()
+    po.step(1)
+    rate = w.nx * probe_rows / max(time.perf_counter() - t0, 1e-6)
+    del po
+    rows = int(np.clip(round(120.0 * rate / (w.nx * total)), 4, w.ny))
     y0 = int(np.clip(int(w.cy) - rows // 2, 0, w.ny - rows))
     band = W.Workload(**{**w.__dict__, "ny": rows, "cy": w.cy - y0})
     fields = {k: np.ascontiguousarray(v[y0:y0 + rows]) for k, v in full.items()}
@@ -254,7 +276,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     mlups = band.nx * band.ny * args.steps / dt / 1e6
     sample = (f"{band.nx}x{band.ny} band (rows {y0}..{y0 + rows - 1}) of {w.name}, "
-              f"periodic, one FP64 oracle step per bench step")
+              f"periodic, one FP64 oracle step per bench step, {cores} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -262,7 +284,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "grid": [w.nx, w.ny], "lattices": w.lattices,
                    "sample_rows": rows},
-        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -454,10 +476,10 @@ def run_ours(args):
     lat2.sync()
     barrier(dist)
     t0 = time.perf_counter()
-    lat2.set_fields(**host)                       # H2D of the initial moments
+    lat2.set_fields(**host)                       # H2D of the initial moments (FP64)
     lat2.step(args.steps)
     st2 = lat2.stats()                            # D2H of the FP64 diagnostics
-    lat2.field(lbmice.PHI)                        # D2H of the result field
+    lat2.field(lbmice.PHI, out=out_phi)           # D2H of the result field, pinned
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(dist, e2e_s)
     h2d = sum(v.nbytes for v in host.values())
@@ -504,11 +526,13 @@ def run_ours(args):
     traffic, rec = profiled_traffic(nodes)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
+                "frac_nominal": achieved / NOMINAL_HBM_GBS,
+                "nominal_peak": NOMINAL_HBM_GBS,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs copy bandwidth)"
                 if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_lup": ALGO_BYTES_PER_LUP[("f32", w.lattices)],
                 "design_bytes_per_lup": DESIGN_BYTES_PER_LUP[("f32", w.lattices)],
-                "kernel": "lbmice::step_kernel<32,8,flow,F32>"}
+                "kernel": "lbmice::march_kernel<flow,F32,prefetch>"}
     if rec is not None:
         roofline["traffic_source"] = rec.get("source")
         if traffic is None:
@@ -544,7 +568,7 @@ def run_ours(args):
         batched["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                "frac": ach / peak, "traffic": btraffic,
                                "algorithmic_bytes_per_lup": 224,
-                               "kernel": "lbmice::batch_step_kernel<32,8,flow,F32>"}
+                               "kernel": "lbmice::batch_march_kernel<flow,F32,prefetch>"}
         if brec is not None:
             batched["roofline"]["traffic_source"] = brec.get("source")
         batched["ms_per_step"] = batched.pop("ms") / batched["steps"]
@@ -572,17 +596,24 @@ def run_ours(args):
     # ---- CPU baseline and error against the FP64 oracle, rank 0, N = 1 only ----
     if world == 1 and not args.no_cpu_baseline:
         fields = W.seed_fields(w)
-        o, n, dt = oracle_run(w, fields, args.cpu_seconds)
+        cores = host_cores()
+        o1, n1, dt1 = oracle_run(w, fields, 0.0, min_steps=2, threads=1)
+        del o1
+        o, n, dt = oracle_run(w, fields, args.cpu_seconds, min_steps=4, threads=cores)
         lat.set_fields(**fields)
         lat.step(n)
         err = {"steps": n,
                "max_dphi": float(np.abs(lat.field(lbmice.PHI) - o.field(0)).max()),
                "max_dU": float(np.abs(lat.field(lbmice.U) - o.field(1)).max()),
                "max_dux": float(np.abs(lat.field(lbmice.UX) - o.field(3)).max())}
-        line["cpu_baseline"] = {"value": nodes * n / dt / 1e6, "unit": "MLUPS", "cores": 1,
+        line["cpu_baseline"] = {"value": nodes * n / dt / 1e6, "unit": "MLUPS", "cores": cores,
                                 "kind": "oracle",
                                 "sample": f"{n} full-grid FP64 oracle steps of {w.name} "
-                                          f"from its seed state, single thread"}
+                                          f"from its seed state, rows split over {cores} "
+                                          f"host threads",
+                                "single_thread": {"value": nodes * n1 / dt1 / 1e6,
+                                                  "unit": "MLUPS", "cores": 1,
+                                                  "sample": f"{n1} full-grid steps, one thread"}}
         line["oracle_error"] = err
         ophi, oU = o.field(0), o.field(1)
         for st, leg in legs.items():

@@ -45,8 +45,8 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, _SRC]
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-o", tmp, _SRC]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -66,6 +66,10 @@ def lib():
         L.orc_derived.argtypes = [vp, dp]
         L.orc_set_fields.argtypes = [vp, dp, dp, dp, dp, dp]
         L.orc_step.argtypes = [vp, i64]
+        L.orc_round_f32.argtypes = [vp]
+        L.orc_set_threads.argtypes = [i32]
+        L.orc_set_threads.restype = i32
+        L.orc_set_threads(1)
         L.orc_steps_done.argtypes = [vp]
         L.orc_steps_done.restype = i64
         L.orc_get_field.argtypes = [vp, i32, dp]
@@ -82,6 +86,12 @@ def lib():
                                    [i64, dp, dp, i32, dp, dp])
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's node loops (rows split statically; results are
+    bit-identical for any count). Returns the count in use."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _dp(a):
@@ -168,6 +178,12 @@ class Oracle:
         a = _f64(arr)
         if lib().orc_set_pops(self._h, int(lattice), _dp(a)):
             raise RuntimeError("orc_set_pops failed")
+
+    def round_to_float32(self) -> None:
+        """Test option: round every population and the phi history to float32 in place (the
+        storage precision of an FP32 run); the next step computes in double as always."""
+        if lib().orc_round_f32(self._h):
+            raise RuntimeError("orc_round_f32 failed")
 
     def post_collision(self, lattice: int) -> np.ndarray:
         shape = (self.ny, self.nx) if lattice == LAT_AS2 else (9, self.ny, self.nx)

@@ -11,6 +11,9 @@
 //   collide every node (Sec. 2.2.1 flow BGK + drag, Sec. 2.2.2 ADR for U, Sec. 2.2.3 Eq. (d)
 //   for phi), then stream every population (pull), then rotate the phi history.
 // All arithmetic is double, compiled with -O2 -ffp-contract=off and without -ffast-math.
+// The node loops of a sweep may run on several host threads (OpenMP, rows split statically,
+// orc_set_threads): every node writes only its own outputs and nothing is summed across
+// nodes, so the results are bit-identical to one thread's.
 //
 // Readings of passages the paper leaves open (each is listed with its reason in the design
 // notes of the repository):
@@ -46,6 +49,8 @@
 // Parity is pinned by tests/test_oracle_pins.py, tests/test_oracle_grad_pins.py and
 // tests/test_oracle_variant_pins.py (closed forms, invariants, symmetries,
 // brute force); no function here is unpinned.
+
+#include <omp.h>
 
 #include <algorithm>
 #include <cmath>
@@ -359,8 +364,9 @@ void alloc(Oracle<T>* o) {
 template <class T>
 void phi_field(const Oracle<T>& o, std::vector<T>* phi) {
   phi->resize(o.n);
-  T v[9];
-  for (size_t i = 0; i < o.n; ++i) {
+#pragma omp parallel for schedule(static)
+  for (long long i = 0; i < (long long)o.n; ++i) {
+    T v[9];
     for (int a = 0; a < 9; ++a) v[a] = o.h[a][i];
     (*phi)[i] = sum9(v);
   }
@@ -412,6 +418,7 @@ void collide(Oracle<T>* o) {
   phi_field(*o, &phi);
   if (o->phi_force)
     for (size_t i = 0; i < o->n; ++i) set_value(phi[i], o->phi_force[i]);
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < o->ny; ++y) {
     for (int x = 0; x < o->nx; ++x) {
       const size_t i = o->at(x, y);
@@ -515,6 +522,7 @@ void source_values(const Oracle<T>& o, int a, int sx, int sy, T* fsv, T* gsv, T*
 //   h_a(y, t+1) = h_a(y, t) + [h*_a(x) - h_a(y, t)] / a_s^2(x).
 template <class T>
 void stream(Oracle<T>* o) {
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < o->ny; ++y) {
     for (int x = 0; x < o->nx; ++x) {
       const size_t i = o->at(x, y);
@@ -728,6 +736,12 @@ int orc_set_fields(void* h, const double* phi, const double* U, const double* rh
   return 0;
 }
 
+// Host threads of the node loops (1 by default); returns the number in use.
+int orc_set_threads(int n) {
+  omp_set_num_threads(n < 1 ? 1 : n);
+  return omp_get_max_threads();
+}
+
 int orc_step(void* h, int64_t nsteps) {
   if (!h || nsteps < 0) return -1;
   OracleD* o = static_cast<OracleD*>(h);
@@ -763,6 +777,26 @@ int orc_set_pops(void* h, int lattice, const double* in) {
   if (lattice == 0 && !o->p.flow) return -1;
   std::vector<double>* dst = lattice == 0 ? o->f : lattice == 1 ? o->g : o->h;
   for (int a = 0; a < 9; ++a) std::memcpy(dst[a].data(), in + a * o->n, o->n * sizeof(double));
+  return 0;
+}
+
+// Test option: round the state (every population and the phi history) to float32 in place,
+// the storage precision of an FP32 run, leaving the arithmetic of the next step in double.
+int orc_round_f32(void* h) {
+  if (!h) return -1;
+  OracleD* o = static_cast<OracleD*>(h);
+  std::vector<double>* lat[3] = {o->f, o->g, o->h};
+  for (int L = 0; L < 3; ++L) {
+    if (L == 0 && !o->p.flow) continue;
+    for (int a = 0; a < 9; ++a) {
+      double* v = lat[L][a].data();
+#pragma omp parallel for schedule(static)
+      for (long long i = 0; i < (long long)o->n; ++i) v[i] = (double)(float)v[i];
+    }
+  }
+  double* ph = o->phi_prev.data();
+#pragma omp parallel for schedule(static)
+  for (long long i = 0; i < (long long)o->n; ++i) ph[i] = (double)(float)ph[i];
   return 0;
 }
 

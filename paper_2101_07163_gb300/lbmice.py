@@ -235,8 +235,16 @@ class Lattice:
 
     # -- outputs --------------------------------------------------------------------------
     def field(self, which: int, out=None):
-        """One moment field as float32. ``out`` may be a CUDA tensor (asynchronous);
-        without it a host numpy array is returned."""
+        """One moment field as float32. ``out`` may be a CUDA tensor (asynchronous) or a
+        C-contiguous float32 numpy array of shape (ny, nx), pinned or pageable, which is
+        filled and returned; without it a new host numpy array is returned."""
+        if isinstance(out, np.ndarray):
+            if (out.dtype != np.float32 or out.shape != (self.ny, self.nx)
+                    or not out.flags["C_CONTIGUOUS"]):
+                raise ValueError("out must be a C-contiguous float32 array of shape (ny, nx)")
+            _check(lib().lbmice_fields(self._h, int(which), _ptr_host(out), out.nbytes, 0),
+                   "lbmice_fields")
+            return out
         if out is not None:
             if out.numel() * 4 < self.nx * self.ny or out.dtype.itemsize != 4:
                 raise ValueError("out must be a float32 tensor of nx*ny elements")

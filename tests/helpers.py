@@ -1,4 +1,6 @@
-"""Test-side helpers: golden-file parsing and contour measurements (no LB arithmetic)."""
+"""Test-side helpers: golden-file parsing, contour measurements and the oracle's host thread
+count (no LB arithmetic)."""
+import contextlib
 import os
 from fractions import Fraction
 
@@ -60,3 +62,16 @@ def tip_x(phi, row, cx, direction=+1):
     if not (0 <= j < len(line)):
         return np.nan
     return i + direction * line[i] / (line[i] - line[j])
+
+
+@contextlib.contextmanager
+def oracle_threads(n=None):
+    """Run the oracle's node loops on n host threads (default: every CPU this process may
+    use) inside the block; its results are bit-identical for any count."""
+    import oracle
+    n = n or len(os.sched_getaffinity(0))
+    oracle.set_threads(n)
+    try:
+        yield n
+    finally:
+        oracle.set_threads(1)

@@ -651,3 +651,47 @@ def test_ghost_rules_at_channel_faces():
             assert f1[a, j, x] == fs[a, js, x]
             lhs = a2[js, x] * h1[a, j, x] + (1 - a2[js, x]) * h0[a, j, x]
             assert lhs == pytest.approx(hs[a, js, x], abs=1e-14)
+
+
+# ------------------------------------------------------------------------------------------
+# Threaded node loops: the timing baseline on all host cores computes the same bits
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("faces", ["periodic", "channel"])
+def test_threaded_oracle_is_bit_identical_to_one_thread(faces):
+    # Rows are split across threads; no node reads another's outputs within a sweep and
+    # nothing is summed across nodes, so every population must come out bit for bit equal.
+    bc = ((W.BC_PERIODIC,) * 4 if faces == "periodic"
+          else (W.BC_INLET, W.BC_OUTLET, W.BC_FREESLIP, W.BC_FREESLIP))
+    w = W.Workload("threads", 61, 47, 6, flow=True, eps=0.05, D=2.0, U0=0.3, nu=0.05,
+                   cx=30.0, cy=23.0, R0=7.0, bc=bc, u_in=0.02, U_in=0.3)
+    f = W.perturbed_fields(w, 2024)
+    runs = []
+    for threads in (1, 4):
+        oracle.set_threads(threads)
+        try:
+            o = Oracle(nx=w.nx, ny=w.ny, **w.params())
+            o.set_fields(**f)
+            o.step(w.steps)
+            runs.append([o.pops(L) for L in (LAT_F, LAT_G, LAT_H)] + [o.field(PHI_PREV)])
+        finally:
+            oracle.set_threads(1)
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+
+
+def test_float32_rounding_option_rounds_the_state_only():
+    # The storage-floor runs of the parity tests round the state to float32 after each step:
+    # populations and the phi history become the nearest float32, nothing else changes.
+    w = W.Workload("r32", 24, 20, 1, flow=True, eps=0.05, D=2.0, U0=0.3, nu=0.05,
+                   cx=12.0, cy=10.0, R0=5.0)
+    o = Oracle(nx=w.nx, ny=w.ny, **w.params())
+    o.set_fields(**W.perturbed_fields(w, 5))
+    o.step(2)
+    before = [o.pops(L) for L in (LAT_F, LAT_G, LAT_H)] + [o.field(PHI_PREV)]
+    o.round_to_float32()
+    after = [o.pops(L) for L in (LAT_F, LAT_G, LAT_H)] + [o.field(PHI_PREV)]
+    for b, a in zip(before, after):
+        assert np.array_equal(a, b.astype(np.float32).astype(np.float64))
+        assert not np.array_equal(a, b)
+    assert o.steps_done == 2
