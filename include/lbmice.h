@@ -180,6 +180,20 @@ int lbmice_load(lbmice_t* h, int32_t which, const void* src, size_t bytes,
  * Synchronises the stream. Errors: EINVAL, ECUDA. */
 int lbmice_stats(lbmice_t* h, double out[LBMICE_NSTATS]);
 
+/* Tip positions (Sec. 3.1.2 measures the tip speed V as the rate of the phi = 0 crossing;
+ * Sec. 3.2.2 compares the tips facing and leaving the inflow), computed on the device from
+ * the current phi, so a long run tracks its tips without exporting the field. For each of
+ * nrays directions angles_deg[i] (degrees, counter-clockwise from +x; host array), radii[i]
+ * (host) receives the distance in cells from (cx, cy) (node coordinates) to the first
+ * crossing of phi from > 0 to <= 0 along the ray: phi is sampled at r = k step, k = 0, 1, ...
+ * by bilinear interpolation of the four surrounding nodes (in double), and the crossing is
+ * placed by linear interpolation between the two samples around it. NaN when phi <= 0 at the
+ * centre, or when the ray reaches x < 0, y < 0, x > nx - 2 or y > ny - 2 first. 1 <= nrays
+ * <= LBMICE_MAX_RAYS, step > 0. Synchronises the stream. Errors: EINVAL, ECUDA. */
+#define LBMICE_MAX_RAYS 1024
+int lbmice_tips(lbmice_t* h, double cx, double cy, double step, int32_t nrays,
+                const double* angles_deg, double* radii);
+
 /* Size in bytes of the LBMICE_FIELD_STATE blob of this handle (0 for a null handle). */
 size_t lbmice_state_bytes(const lbmice_t* h);
 
@@ -339,8 +353,11 @@ int lbmice_tape_destroy(lbmice_tape_t* t);
  *   stream:   cudaStream_t the work is enqueued on (asynchronous; nothing is synchronised).
  * Grids of more than LBMICE_NOALLOC_MAX_NODES nodes are rejected with LBMICE_EINVAL, as are
  * null pointers and pitch < nx. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture. Every call uses the same array, which keeps the last call's partial sums (no element
+ * (cudaGetSymbolAddress) with that device current and caches it per device ordinal for the
+ * life of the process; make that first call before any stream capture. The cached address
+ * belongs to the device's primary context as it was then: after cudaDeviceReset (or anything
+ * else that destroys and recreates that context) it is stale and this entry point must not
+ * be called again in the process. Every call uses the same array, which keeps the last call's partial sums (no element
  * needs to start at zero): calls that overlap on the GPU -- on different streams, or from
  * different threads -- race on it and must be serialised by the caller.
  * Errors: EINVAL, ECUDA. */

@@ -39,10 +39,11 @@ class Rollout(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, g):
+        # The tape may be swept again (backward with retain_graph=True, then another
+        # backward); its checkpoints and the grid are freed with the autograd graph that
+        # holds ctx.
         dphi, scalar_U, dU, deps, dD = ctx.meta
         grads, fields = ctx.tape.backward(phi_bar=g.detach().contiguous())
-        ctx.tape.close()
-        ctx.lat.close()
         gU = fields["U0"].sum() if scalar_U else fields["U0"]
         dev = g.device
         return (fields["phi0"].to(dphi), gU.to(dU),

@@ -53,6 +53,8 @@ struct lbmice_ctx {
   double* stat_partial = nullptr;
   double* stat_out = nullptr;
   double* stat_host = nullptr;     // pinned
+  double* tip_dev = nullptr;       // (cos, sin) of up to LBMICE_MAX_RAYS rays, then their radii
+  double* tip_host = nullptr;      // pinned, the same layout
   cudaGraphExec_t graph = nullptr;
   int64_t step = 0;
   // tensor maps of the march's L2 prefetch, kMapsPerPhase per step phase (step mod 6), in
@@ -149,6 +151,8 @@ void release(lbmice_t* h) {
   if (h->stat_partial) cudaFree(h->stat_partial);
   if (h->stat_out) cudaFree(h->stat_out);
   if (h->stat_host) cudaFreeHost(h->stat_host);
+  if (h->tip_dev) cudaFree(h->tip_dev);
+  if (h->tip_host) cudaFreeHost(h->tip_host);
   if (h->tmaps) cudaFree(h->tmaps);
   if (h->capture) cudaStreamDestroy(h->capture);
   delete h;
@@ -443,6 +447,8 @@ int lbmice_create(const lbmice_params* p, void* stream, lbmice_t** out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->stat_partial, sizeof(double) * kStatBlocks * kNStat);
   if (e == cudaSuccess) e = cudaMalloc(&h->stat_out, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMallocHost(&h->stat_host, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&h->tip_dev, sizeof(double) * 3 * LBMICE_MAX_RAYS);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->tip_host, sizeof(double) * 3 * LBMICE_MAX_RAYS);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i)
     e = cudaMemsetAsync(h->pops[i], 0, pop_bytes(h), h->stream);
   for (int i = 0; i < 3 && e == cudaSuccess; ++i)
@@ -706,6 +712,32 @@ int lbmice_stats(lbmice_t* h, double out[LBMICE_NSTATS]) {
   return LBMICE_OK;
 }
 
+int lbmice_tips(lbmice_t* h, double cx, double cy, double step, int32_t nrays,
+                const double* angles_deg, double* radii) {
+  if (!h || !angles_deg || !radii || nrays < 1 || nrays > LBMICE_MAX_RAYS ||
+      !(step > 0.0) || !std::isfinite(step) || !std::isfinite(cx) || !std::isfinite(cy))
+    return LBMICE_EINVAL;
+  const double deg = 3.14159265358979323846 / 180.0;
+  for (int i = 0; i < nrays; ++i) {
+    if (!std::isfinite(angles_deg[i])) return LBMICE_EINVAL;
+    h->tip_host[2 * i] = std::cos(angles_deg[i] * deg);
+    h->tip_host[2 * i + 1] = std::sin(angles_deg[i] * deg);
+  }
+  double* cs = h->tip_dev;
+  double* out = h->tip_dev + 2 * LBMICE_MAX_RAYS;
+  LB_TRY(cudaMemcpyAsync(cs, h->tip_host, sizeof(double) * 2 * nrays, cudaMemcpyHostToDevice,
+                         h->stream));
+  const int per_block = 8;  // rays (warps) per block
+  tips_kernel<<<(nrays + per_block - 1) / per_block, 32 * per_block, 0, h->stream>>>(
+      h->phi[h->step % 3], h->C.nx, h->C.ny, h->C.pitch, cx, cy, step, nrays, cs, out);
+  LB_TRY(cudaGetLastError());
+  LB_TRY(cudaMemcpyAsync(h->tip_host + 2 * LBMICE_MAX_RAYS, out, sizeof(double) * nrays,
+                         cudaMemcpyDeviceToHost, h->stream));
+  LB_TRY(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < nrays; ++i) radii[i] = h->tip_host[2 * LBMICE_MAX_RAYS + i];
+  return LBMICE_OK;
+}
+
 int lbmice_sync(lbmice_t* h) {
   if (!h) return LBMICE_EINVAL;
   LB_TRY(cudaStreamSynchronize(h->stream));
@@ -797,7 +829,8 @@ std::atomic<double*> g_noalloc_ptr[kNoallocMaxDevices];
 
 // Device address of the fixed array on the current device. Host code only holds a host-side
 // stand-in for the symbol, so the address is asked for once per device, with that device
-// current, and cached.
+// current, and cached for the life of the process (valid while the device's primary context
+// lives: a cudaDeviceReset makes it stale, as the header states).
 int noalloc_scratch(double** out) {
   int dev = 0;
   LB_TRY(cudaGetDevice(&dev));

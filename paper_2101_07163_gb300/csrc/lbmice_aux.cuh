@@ -234,4 +234,47 @@ __global__ void stats_final_kernel(const double* __restrict__ partial, int nbloc
   }
 }
 
+// Tip positions: one warp per ray; the lanes evaluate 32 consecutive samples r = k step at a
+// time and the first event along the ray (leaving the box [0, nx - 2] x [0, ny - 2], phi <= 0
+// at the centre, or a crossing of phi from > 0 to <= 0) decides the result. phi is a
+// [ny][pitch] plane; cs holds (cos, sin) of each ray's angle.
+__device__ __forceinline__ double tip_bilinear(const float* __restrict__ phi, int pitch,
+                                               double x, double y) {
+  const int i = (int)x, j = (int)y;
+  const double fx = x - i, fy = y - j;
+  const float* p = phi + (long long)j * pitch + i;
+  return ((double)p[0] * (1 - fx) + (double)p[1] * fx) * (1 - fy) +
+         ((double)p[pitch] * (1 - fx) + (double)p[pitch + 1] * fx) * fy;
+}
+
+__global__ void tips_kernel(const float* __restrict__ phi, int nx, int ny, int pitch, double cx,
+                            double cy, double step, int nrays, const double* __restrict__ cs,
+                            double* __restrict__ radii) {
+  const int ray = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (ray >= nrays) return;
+  const double c = cs[2 * ray], s = cs[2 * ray + 1];
+  double carry = 0.0;  // phi at the last sample of the previous group of 32
+  for (long long base = 0;; base += 32) {
+    const long long k = base + lane;
+    const double r = (double)k * step;
+    const double x = cx + r * c, y = cy + r * s;
+    const bool outside = !(x >= 0.0 && y >= 0.0 && x <= nx - 2 && y <= ny - 2);
+    const double v = outside ? 0.0 : tip_bilinear(phi, pitch, x, y);
+    double pv = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) pv = carry;
+    const bool start_out = k == 0 && !outside && v <= 0.0;
+    const bool cross = k > 0 && !outside && pv > 0.0 && v <= 0.0;
+    const unsigned m = __ballot_sync(0xffffffffu, outside || start_out || cross);
+    if (m) {
+      if (lane == __ffs(m) - 1) {
+        const double prev_r = (double)(k - 1) * step;
+        radii[ray] = cross ? prev_r + (r - prev_r) * pv / (pv - v) : __longlong_as_double(0x7ff8000000000000LL);
+      }
+      return;
+    }
+    carry = __shfl_sync(0xffffffffu, v, 31);
+  }
+}
+
 }  // namespace lbmice

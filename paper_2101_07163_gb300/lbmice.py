@@ -21,6 +21,7 @@ BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FREESLIP = 0, 1, 2, 3
 PHI, U, RHO, UX, UY, PHI_PREV, POPS, STATE = 0, 1, 2, 3, 4, 5, 6, 7
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 NSTATS = 6
+MAX_RAYS = 1024  # LBMICE_MAX_RAYS
 STAT_NAMES = ("area", "mass", "vapour_invariant", "sum_phi", "nonfinite", "steps")
 
 EXPORTS = ("lbmice_params_default", "lbmice_create", "lbmice_init_seed", "lbmice_set_fields",
@@ -31,7 +32,7 @@ EXPORTS = ("lbmice_params_default", "lbmice_create", "lbmice_init_seed", "lbmice
            "lbmice_batch_set_shape", "lbmice_batch_destroy", "lbmice_last_error",
            "lbmice_tape_create", "lbmice_tape_record", "lbmice_tape_steps",
            "lbmice_tape_backward", "lbmice_tape_destroy", "lbmice_debug_flags",
-           "lbmice_debug_set_margin")
+           "lbmice_debug_set_margin", "lbmice_tips")
 
 
 class LbmiceError(RuntimeError):
@@ -109,6 +110,8 @@ def lib():
         L.lbmice_tape_destroy.argtypes = [vp]
         L.lbmice_debug_flags.argtypes = [ctypes.POINTER(ctypes.c_uint32), i32]
         L.lbmice_debug_set_margin.argtypes = [i64]
+        L.lbmice_tips.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32,
+                                  dp, dp]
         _lib = L
     return _lib
 
@@ -278,6 +281,17 @@ class Lattice:
     def load_state(self, blob: np.ndarray):
         a = np.ascontiguousarray(blob, dtype=np.uint8)
         _check(lib().lbmice_load(self._h, STATE, _ptr_host(a), a.nbytes, 0), "lbmice_load")
+
+    def tips(self, cx: float, cy: float, angles_deg, step: float = 0.25) -> np.ndarray:
+        """Distance from (cx, cy) to the first phi = 0 crossing along each ray (degrees),
+        computed on the device from the current phi (include/lbmice.h, lbmice_tips)."""
+        a = np.ascontiguousarray(np.atleast_1d(angles_deg), dtype=np.float64)
+        out = np.empty_like(a)
+        _check(lib().lbmice_tips(self._h, float(cx), float(cy), float(step), int(a.size),
+                                 a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "lbmice_tips")
+        return out
 
     def stats(self) -> dict:
         out = (ctypes.c_double * NSTATS)()

@@ -203,6 +203,26 @@ def test_rollout_autograd_matches_the_tape():
     assert U0.grad.item() == pytest.approx(float(init["U0"].astype(np.float64).sum()), rel=1e-6)
 
 
+def test_rollout_backward_can_run_twice_on_a_retained_graph():
+    # backward(retain_graph=True) then backward again sweeps the same tape twice: the second
+    # sweep gives the same gradients, which autograd adds to the first
+    import torch
+    from paper_2101_07163_gb300 import adjoint
+    w, f = case(False, nx=36, ny=28)
+    dev = torch.device("cuda")
+    phi0 = torch.tensor(f["phi"], device=dev, requires_grad=True)
+    eps = torch.tensor(w.eps, dtype=torch.float64, device=dev, requires_grad=True)
+    D = torch.tensor(w.D, dtype=torch.float64, device=dev, requires_grad=True)
+    U0 = torch.tensor(0.35, dtype=torch.float64, device=dev, requires_grad=True)
+    loss = (adjoint.rollout(phi0, U0, eps, D, nsteps=23, every=8).double() ** 2).sum()
+    loss.backward(retain_graph=True)
+    first = (eps.grad.item(), D.grad.item(), U0.grad.item(), phi0.grad.clone())
+    loss.backward()
+    assert eps.grad.item() == 2 * first[0] and D.grad.item() == 2 * first[1]
+    assert U0.grad.item() == pytest.approx(2 * first[2], rel=1e-12)
+    assert torch.equal(phi0.grad, 2 * first[3])
+
+
 # ---- the gradient workload: 512^2 periodic, f + g + h, seed R = 6 at the centre, start
 # parameters (U0, eps, D) = (0.3, 0.04, 2.0), target run (0.4, 0.06, 2.5), 3000 steps,
 # checkpoints every 100 steps -------------------------------------------------------------

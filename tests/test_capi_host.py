@@ -91,6 +91,7 @@ def test_null_handles_are_rejected(L):
     assert L.lbmice_stats(None, None) == lbmice.EINVAL
     assert L.lbmice_set_fields(None, None, None, None, None, None, 0) == lbmice.EINVAL
     assert L.lbmice_sync(None) == lbmice.EINVAL
+    assert L.lbmice_tips(None, 0.0, 0.0, 0.25, 1, None, None) == lbmice.EINVAL
     assert L.lbmice_steps_done(None) == -1
     assert L.lbmice_state_bytes(None) == 0
     assert L.lbmice_destroy(None) == 0

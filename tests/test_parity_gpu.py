@@ -320,6 +320,34 @@ def test_stats_match_oracle_reductions():
     assert s["vapour_invariant"] == pytest.approx(s0["vapour_invariant"], rel=1e-5)
 
 
+def test_device_tips_equal_host_diagnostics_and_follow_the_oracle():
+    # lbmice_tips applies the definition of diagnostics.tip_radius on the device: on the same
+    # exported field the two agree to rounding; against the FP64 oracle's field the tips of
+    # the FP32 run lie within 2e-3 cells (phi differs by ~4e-5 where |grad phi| ~ 0.3/cell).
+    from paper_2101_07163_gb300 import diagnostics as D
+    w = W.C3.with_size(160, 160)
+    lat, orc = pair(w, W.seed_fields(w))
+    lat.step(1500)
+    orc.step(1500)
+    angles = np.arange(0.0, 360.0, 15.0)
+    dev = lat.tips(w.cx, w.cy, angles)
+    phi = lat.field(lbmice.PHI).astype(np.float64)
+    host = np.array([D.tip_radius(phi, w.cx, w.cy, a) for a in angles])
+    assert np.all(np.isfinite(dev)) and dev.min() > w.R0
+    assert np.abs(dev - host).max() < 1e-9
+    ophi = orc.field(oracle.PHI)
+    ref = np.array([D.tip_radius(ophi, w.cx, w.cy, a) for a in angles])
+    assert np.abs(dev - ref).max() < 2e-3
+    # a centre outside the crystal, and a ray that leaves the grid first: NaN
+    assert np.isnan(lat.tips(3.0, 3.0, [0.0])[0])
+    assert np.isnan(lat.tips(w.cx, w.cy, [0.0], step=1000.0)[0])
+    assert np.isnan(D.tip_radius(phi, w.cx, w.cy, 0.0, step=1000.0))
+    with pytest.raises(lbmice.LbmiceError):
+        lat.tips(w.cx, w.cy, [0.0], step=0.0)
+    with pytest.raises(lbmice.LbmiceError):
+        lat.tips(w.cx, w.cy, np.zeros(lbmice.MAX_RAYS + 1))
+
+
 def test_nonfinite_state_is_reported_not_trapped():
     w = channel_workload("n", 64, 40, (W.BC_PERIODIC,) * 4)
     f = W.perturbed_fields(w, 16)

@@ -69,6 +69,44 @@ def test_noalloc_stats_match_stats_on_two_calls_in_a_row():
     assert not np.array_equal(seen[0], seen[1])
 
 
+def padded(t, pitch, torch):
+    """t (..., ny, nx) copied into rows of pitch floats; the padding holds NaN, which a sum
+    that read it would carry into its result."""
+    p = torch.full(tuple(t.shape[:-1]) + (pitch,), float("nan"), device="cuda",
+                   dtype=torch.float32)
+    p[..., :t.shape[-1]] = t
+    return p.contiguous()
+
+
+@pytest.mark.parametrize("flow", [True, False])
+def test_noalloc_reads_padded_rows_with_and_without_flow(flow):
+    # Rows of pitch = nx + 13 floats (plane stride pitch * ny), and a grid without the flow
+    # lattice (18 planes; the mass is then the node count): the same five values as
+    # lbmice_stats.
+    torch = pytest.importorskip("torch")
+    w = W.Workload("noalloc_pad", 150, 77, 1, flow=flow, eps=0.05, D=2.0, U0=0.35, nu=0.05,
+                   cx=70.0, cy=40.0, R0=9.0)
+    lat = lbmice.Lattice(w.nx, w.ny, **w.params())
+    lat.set_fields(**W.perturbed_fields(w, 33))
+    lat.step(12)
+    ref = lat.stats()
+    pops, phi, prev = export_state(lat, torch)
+    pitch = w.nx + 13
+    pp, ph, pv = padded(pops, pitch, torch), padded(phi, pitch, torch), padded(prev, pitch, torch)
+    out = torch.full((5,), -1.0, device="cuda", dtype=torch.float64)
+    rc = noalloc_fn()(ctypes.c_void_p(pp.data_ptr()), ctypes.c_void_p(ph.data_ptr()),
+                      ctypes.c_void_p(pv.data_ptr()), w.nx, w.ny, pitch, 1 if flow else 0,
+                      w.dx, w.L_sat, ctypes.c_void_p(out.data_ptr()),
+                      ctypes.c_void_p(lat.stream.cuda_stream))
+    assert rc == lbmice.OK, lbmice.strerror(rc)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for k, name in enumerate(NAMES):
+        assert got[k] == pytest.approx(ref[name], rel=1e-12, abs=1e-9), (flow, name)
+    if not flow:
+        assert got[1] == w.nx * w.ny
+
+
 def test_noalloc_rejects_grids_beyond_its_fixed_array():
     fn = noalloc_fn()
     dummy = ctypes.c_void_p(16)  # never dereferenced: the size check comes first
