@@ -63,6 +63,8 @@ def parse():
                     help="steps of the gradient workload leg (512^2, adjoint; 0: skip)")
     ap.add_argument("--grad-n", type=int, default=512,
                     help="grid side of the gradient leg (profiling runs only)")
+    ap.add_argument("--grad-large-steps", type=int, default=300,
+                    help="steps of the gradient leg at twice the side, beyond L2 (0: skip)")
     return ap.parse_args()
 
 
@@ -352,21 +354,27 @@ def run_batched(args, stream, dist, rank: int = 0, world: int = 1):
     return out
 
 
-# Bytes per node of one reverse step as built: the collision adjoint reads the state (27
-# populations, phi^n, phi^{n-1}) and the adjoint (27 + 2 planes) and writes 27 + 5 planes
-# (360 B); the pull adjoint reads 9 + 9 population planes and 6 planes, writes 9 + 1 (132 B);
-# recomputing the segment's forward states adds one step (228 B).
-REVERSE_BYTES_PER_NODE = 360 + 132 + 228
+# Bytes per node of one reverse step. Algorithmic (what the method itself must move): the
+# state it differentiates read (27 populations, phi^n, phi^{n-1}: 116 B), the adjoint of the
+# next state read (116 B) and the adjoint of this state written (116 B), plus, under
+# checkpointing, one recomputed forward step (224 B). As built: the collision adjoint reads
+# the state (27 populations, phi^n, phi^{n-1}) and the adjoint (27 + 2 planes) and writes
+# 27 + 5 planes (360 B); the pull adjoint reads 9 + 9 population planes and 6 planes, writes
+# 9 + 1 (132 B); the recomputed step moves 228 B.
+REVERSE_ALGO_BYTES_PER_NODE = 3 * 116 + 224
+REVERSE_DESIGN_BYTES_PER_NODE = 360 + 132 + 228
 
 
-def run_gradient(args, stream, dist):
-    """The gradient workload: 512^2 periodic, f + g + h, seed R = 6 at the centre, from
+def run_gradient(args, stream, dist, n=None, steps=None, fd=True):
+    """The gradient workload: n^2 periodic (512^2), f + g + h, seed R = 6 at the centre, from
     (U0, eps, D) = (0.3, 0.04, 2.0) towards the run of (0.4, 0.06, 2.5), checkpoints every
     100 steps; L = sum (phi_T - phi_T^target)^2. Times the recorded forward and the reverse
-    sweep, and checks the gradient against central differences (h = 1e-3)."""
+    sweep, and (fd) checks the gradient against central differences (h = 1e-3)."""
     import torch
     from paper_2101_07163_gb300 import lbmice
-    n, steps, every = args.grad_n, args.grad_steps, 100
+    n = n or args.grad_n
+    steps = steps or args.grad_steps
+    every = 100
     w = W.Workload("grad", n, n, steps, flow=True, eps=0.04, D=2.0, U0=0.3, cx=n / 2,
                    cy=n / 2, R0=6.0)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -410,28 +418,37 @@ def run_gradient(args, stream, dist):
     g = {"U0": float(fields["U0"].double().sum()), "eps": grads["eps"], "D": grads["D"]}
     tape.close()
     lat.close()
-    h = 1e-3
-    base = {"U0": 0.3, "eps": 0.04, "D": 2.0}
-    fd, rel = {}, {}
-    for k, v in base.items():
-        up = float(((phi_T(**dict(base, **{k: v + h})) - target) ** 2).sum())
-        dn = float(((phi_T(**dict(base, **{k: v - h})) - target) ** 2).sum())
-        fd[k] = (up - dn) / (2 * h)
-        rel[k] = abs(g[k] - fd[k]) / abs(fd[k])
     nodes = n * n
     peak, _ = measured_peak()
-    ach = REVERSE_BYTES_PER_NODE * nodes * steps / (bwd_ms * 1e-3) / 1e9
-    return {"workload": "gradient %dx%d periodic f+g+h, %d steps, checkpoints every 100"
-                        % (n, n, steps),
-            "loss": L0, "gradient": g, "central_differences_h1e-3": fd, "rel_err_vs_fd": rel,
-            "forward_recorded_ms": fwd_ms, "reverse_ms": bwd_ms,
-            "reverse_mlups": nodes * steps / (bwd_ms * 1e-3) / 1e6,
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": ach / peak, "bytes_per_node_reverse_step":
-                             REVERSE_BYTES_PER_NODE,
-                         "kernels": "adj_collide_kernel + adj_pull_kernel + step_kernel "
-                                    "(segment recompute)"},
-            "gpu_launches_per_reverse_step": 3}
+    ach = REVERSE_ALGO_BYTES_PER_NODE * nodes * steps / (bwd_ms * 1e-3) / 1e9
+    state_mb = 4 * 116 * nodes / 1e6  # state and adjoint, read and written, per step
+    out = {"workload": "gradient %dx%d periodic f+g+h, %d steps, checkpoints every 100"
+                       % (n, n, steps),
+           "loss": L0, "gradient": g,
+           "forward_recorded_ms": fwd_ms, "reverse_ms": bwd_ms,
+           "reverse_mlups": nodes * steps / (bwd_ms * 1e-3) / 1e6,
+           "l2_resident": state_mb < 129.0,
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                        "frac": ach / peak,
+                        "algorithmic_bytes_per_node_reverse_step": REVERSE_ALGO_BYTES_PER_NODE,
+                        "design_bytes_per_node_reverse_step": REVERSE_DESIGN_BYTES_PER_NODE,
+                        "frac_design_bytes": REVERSE_DESIGN_BYTES_PER_NODE * nodes * steps
+                                             / (bwd_ms * 1e-3) / 1e9 / peak,
+                        "kernels": "adj_collide_kernel + adj_pull_kernel + march_kernel "
+                                   "(segment recompute)"},
+           "gpu_launches_per_reverse_step": 3}
+    if fd:
+        h = 1e-3
+        base = {"U0": 0.3, "eps": 0.04, "D": 2.0}
+        fdv, rel = {}, {}
+        for k, v in base.items():
+            up = float(((phi_T(**dict(base, **{k: v + h})) - target) ** 2).sum())
+            dn = float(((phi_T(**dict(base, **{k: v - h})) - target) ** 2).sum())
+            fdv[k] = (up - dn) / (2 * h)
+            rel[k] = abs(g[k] - fdv[k]) / abs(fdv[k])
+        out["central_differences_h1e-3"] = fdv
+        out["rel_err_vs_fd"] = rel
+    return out
 
 
 def run_ours(args):
@@ -510,6 +527,10 @@ def run_ours(args):
     gradient = None
     if args.grad_steps > 0:
         gradient = run_gradient(args, stream, dist)
+        if args.grad_large_steps > 0:
+            # the same workload at 1024^2, whose state and adjoint (about 490 MB) exceed L2
+            gradient["beyond_l2"] = run_gradient(args, stream, dist, n=2 * args.grad_n,
+                                                 steps=args.grad_large_steps, fd=False)
 
     if rank != 0:
         for leg in legs.values():

@@ -256,14 +256,21 @@ int with_storage(const lbmice_t* h, Fn&& fn) {
   }
 }
 
-// Launch grid of the march over one grid: one CTA per (strip, segment of rows).
-dim3 march_grid(const Consts& C) {
-  const int H = march_seg_rows(C.ny);
-  return dim3(march_strips(C.nx), (C.ny + H - 1) / H);
+// Segment height of the march for one grid on a device of sms SMs: the tallest of 64, 32, 16
+// rows that still gives one and a half waves of 4 CTAs per SM, else 8. (A batch, which has
+// CTAs enough, walks every member in segments of 64.)
+int march_seg_rows(int nx, int ny, int sms) {
+  for (int H = kMarchMaxSegRows; H > kMarchRows; H /= 2)
+    if ((long long)march_strips(nx) * ((ny + H - 1) / H) >= 6LL * sms) return H;
+  return kMarchRows;
 }
-long long march_units(const Consts& C) {
-  const int H = march_seg_rows(C.ny);
+
+// Launch grid of the march over one grid: one CTA per (strip, segment of H rows).
+long long march_units(const Consts& C, int H) {
   return (long long)march_strips(C.nx) * ((C.ny + H - 1) / H);
+}
+dim3 march_grid(const Consts& C) {
+  return dim3(march_strips(C.nx), (C.ny + C.seg_rows - 1) / C.seg_rows);
 }
 
 // Opt the march kernels of this storage into the shared memory they use (above 48 KB).
@@ -463,6 +470,11 @@ int lbmice_create(const lbmice_params* p, void* stream, lbmice_t** out) {
     cudaGetLastError();  // clear a sticky-free error state left by a failed allocation
     return cuda_err(e);
   }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+      sms < 1)
+    sms = 1;
+  h->C.seg_rows = march_seg_rows(h->C.nx, h->C.ny, sms);
   rc = march_attributes(h);
   if (rc == LBMICE_OK) rc = make_tensor_maps(h);
   if (rc != LBMICE_OK) {
@@ -897,7 +909,7 @@ int64_t batch_steps(const lbmice_batch_t* b) { return b->members[0]->step; }
 
 // Work units of a member in a launch of this shape: tiles, or (strip, row) pairs of the march.
 long long member_units(const lbmice_t* m, int shape) {
-  if (shape == LBMICE_SHAPE_MARCH) return march_units(m->C);
+  if (shape == LBMICE_SHAPE_MARCH) return march_units(m->C, kMarchMaxSegRows);
   const int tx = shape_tx(shape), ty = shape_ty(shape);
   return (long long)((m->C.nx + tx - 1) / tx) * ((m->C.ny + ty - 1) / ty);
 }
@@ -960,6 +972,7 @@ int launch_members(lbmice_batch_t* b, const std::vector<int>& idx, int ph, cudaS
         const lbmice_t* h = b->members[i];
         BatchDesc& d = L.d[L.n];
         d.C = h->C;
+        d.C.seg_rows = kMarchMaxSegRows;
         d.P = step_ptrs(h, ph);
         d.tiles_x = s == LBMICE_SHAPE_MARCH ? march_strips(h->C.nx)
                                             : (h->C.nx + shape_tx(s) - 1) / shape_tx(s);

@@ -327,6 +327,7 @@ struct Consts {
   int bc[4];
   int stencil;        // gradient stencil (Sec. 3.1.1): 2, 4, 6 or 8
   int fold;           // anisotropy symmetry: 6 (ice, Sec. 2.1) or 4 (validation case)
+  int seg_rows;       // rows of the strip segment one march CTA walks (a multiple of 8)
   long long pstride;  // floats between population planes of one node
   long long rstride;  // floats between rows of one population plane
   float Dphi3;       // 3 (W0^2/tau0) dt/dx^2: eta = Dphi3 a_s^2 + 1/2, h^eq flux weight

@@ -798,20 +798,19 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
   }
 }
 
-// Rows of the strip segment a march CTA walks: tall enough that the two extra rows collided
-// where a segment starts cost little, short enough that a launch has many CTAs. CTAs are
-// numbered strip-fastest, so the CTAs resident at one time cover whole bands of rows, and
-// neighbouring strips (which re-read each other's edge columns) run side by side.
-__host__ __device__ constexpr int march_seg_rows(int ny) {
-  return ny < 64 ? ((ny + kMarchRows - 1) / kMarchRows) * kMarchRows : 64;
-}
+// Rows of the strip segment a march CTA walks (Consts::seg_rows, chosen on the host): tall
+// enough that the two extra rows collided where a segment starts cost little, short enough
+// that a launch has a few waves of CTAs. CTAs are numbered strip-fastest, so the CTAs
+// resident at one time cover whole bands of rows, and neighbouring strips (which re-read
+// each other's edge columns) run side by side.
+constexpr int kMarchMaxSegRows = 64;
 
 // One CTA per (strip, segment): blockIdx.x the strip, blockIdx.y the segment. Held to 64
 // registers (4 CTAs of 256 threads per SM).
 template <bool FLOW, class S, int MODE>
 __global__ void __launch_bounds__(kMarchThreads, 4) march_kernel(const Consts C, const StepPtrs P) {
   extern __shared__ __align__(16) float march_smem[];
-  const int H = march_seg_rows(C.ny), r0 = blockIdx.y * H;
+  const int H = C.seg_rows, r0 = blockIdx.y * H;
   march_range<FLOW, S, MODE>(C, P, blockIdx.x * kMarchCols, r0, min(C.ny, r0 + H), march_smem);
 }
 
@@ -880,7 +879,7 @@ __global__ void __launch_bounds__(kMarchThreads, 4) batch_march_kernel(const __g
   const BatchDesc& d = L.d[m];
   const int local = (int)(t - L.tile_start[m]);
   const int seg = local / d.tiles_x, strip = local - seg * d.tiles_x;
-  const int H = march_seg_rows(d.C.ny), r0 = seg * H;
+  const int H = d.C.seg_rows, r0 = seg * H;
   if (local < 0 || r0 >= d.C.ny) return;
   march_range<FLOW, S, MODE>(d.C, d.P, strip * kMarchCols, r0, min(d.C.ny, r0 + H), march_smem);
 }
