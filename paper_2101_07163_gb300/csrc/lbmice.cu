@@ -205,6 +205,9 @@ bool encode_map(CUtensorMap* m, CUtensorMapDataType t, int rank, const void* bas
 // The maps of every step phase (the boxes of one march pass: 8 rows of a strip), encoded on
 // the host and copied to the device once; the buffers never move.
 int make_tensor_maps(lbmice_t* h) {
+  // FP32 storage runs the plain march: prefetching its bandwidth-bound steps measured 15 B
+  // per node of extra DRAM reads and no gain; the issue-bound 16-bit steps gain 3%
+  if (!dev16(h)) return LBMICE_OK;
   std::vector<CUtensorMap> maps(kPhases * kMapsPerPhase);
   std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
   const uint64_t P = h->C.pitch, NY = h->C.ny, Q = h->C.pstride;
@@ -286,8 +289,9 @@ int march_attributes(const lbmice_t* h) {
     set(march_kernel<false, S, MARCH_PREFETCH>, march_smem_bytes<false>());
     set(march_kernel<true, S, MARCH_PLAIN>, march_smem_bytes<true>());
     set(march_kernel<false, S, MARCH_PLAIN>, march_smem_bytes<false>());
-    set(batch_march_kernel<true, S, MARCH_PREFETCH>, march_smem_bytes<true>());
-    set(batch_march_kernel<false, S, MARCH_PREFETCH>, march_smem_bytes<false>());
+    constexpr int M = Storage<S>::DEV ? MARCH_PREFETCH : MARCH_PLAIN;
+    set(batch_march_kernel<true, S, M>, march_smem_bytes<true>());
+    set(batch_march_kernel<false, S, M>, march_smem_bytes<false>());
     return cuda_err(e);
   });
 }
@@ -296,7 +300,7 @@ int march_attributes(const lbmice_t* h) {
 int launch_step_ptrs(const lbmice_t* h, const StepPtrs& P, cudaStream_t st) {
   if (h->C.stencil == 4 && h->C.fold == 6) {
     // the default scheme (E4, six-fold): the column march, its populations prefetched into
-    // L2 by TMA when the step's buffers have tensor maps
+    // L2 by TMA when the step's buffers have tensor maps (16-bit storage)
     const dim3 grid = march_grid(h->C);
     return with_storage(h, [&](auto tag) {
       using S = decltype(tag);
@@ -341,7 +345,7 @@ int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
   P.U_np1 = h->Um[(s + 1) & 1];
   P.rho_n = h->rhom[s & 1];
   P.rho_np1 = h->rhom[(s + 1) & 1];
-  P.tm = h->tmaps + kMapsPerPhase * (s % kPhases);
+  P.tm = h->tmaps ? h->tmaps + kMapsPerPhase * (s % kPhases) : nullptr;
   return launch_step_ptrs(h, P, st);
 }
 
@@ -926,7 +930,7 @@ StepPtrs step_ptrs(const lbmice_t* h, int ph) {
   P.U_np1 = h->Um[(ph + 1) & 1];
   P.rho_n = h->rhom[ph & 1];
   P.rho_np1 = h->rhom[(ph + 1) & 1];
-  P.tm = h->tmaps + kMapsPerPhase * ph;
+  P.tm = h->tmaps ? h->tmaps + kMapsPerPhase * ph : nullptr;
   return P;
 }
 
@@ -947,11 +951,13 @@ int launch_block(const lbmice_batch_t* b, long long tiles, cudaStream_t st) {
 int launch_march_block(const lbmice_batch_t* b, long long units, cudaStream_t st) {
   return with_storage(b->members[0], [&](auto tag) {
     using S = decltype(tag);
+    // members with tensor maps (16-bit storage) prefetch, as their single-grid steps do
+    constexpr int M = Storage<S>::DEV ? MARCH_PREFETCH : MARCH_PLAIN;
     if (b->flow)
-      batch_march_kernel<true, S, MARCH_PREFETCH>
+      batch_march_kernel<true, S, M>
           <<<(unsigned)units, kMarchThreads, march_smem_bytes<true>(), st>>>(*b->block);
     else
-      batch_march_kernel<false, S, MARCH_PREFETCH>
+      batch_march_kernel<false, S, M>
           <<<(unsigned)units, kMarchThreads, march_smem_bytes<false>(), st>>>(*b->block);
     return cuda_err(cudaGetLastError());
   });

@@ -206,10 +206,8 @@ __device__ __forceinline__ float2 sum9_2(const float2* v) {
 //     -k c.u*, f* = c1 f + w (c2 + c3 c.u* + c4 (c.u*)^2) with
 //     c2 = r (1 - 3/2 u*.u*) + 3 gamma k u*.u*, c3 = 3 (r - gamma k), c4 = 9/2 (r - 2 gamma k),
 //     r = rho / tau_f, gamma = 1 - 1/(2 tau_f).
-// h and g are evaluated as pairs (h_a, g_a) with packed FP32x2 operations, f as pairs of
-// directions; opposite directions use exactly negated odd terms, and the weights 1/36 and
-// 4/9 are the weight 1/9 scaled by powers of two, so mirror images of a state stay
-// bit-exact mirror images.
+// The projections c.v are sums and exact negations (cdot), so mirror images of a state stay
+// bit-exact mirror images. (h*_a/a_s^2, g*_a) go to shared memory as one pair.
 template <bool FLOW, class S, bool OWN, int R, class ViewAt>
 __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& P, int X, int Y,
                                                int node, const ViewAt& view_at,
@@ -395,26 +393,17 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     for (int a = 0; a < 9; ++a) hown[a] = ST::DEV ? fmaf(w_of(a), ph, hg[a].x) : hg[a].x;
   }
 
-  // ---- the collision (factored, packed) ----
-  constexpr float wA = 1.0f / 9.0f;
-  float a2 = __fmul_rn(fmaf(ph, inv_eta, srcQ), inv_as2);
-  float b2 = fmaf(U, inv_tg, srcU);
+  // ---- the collision (factored) ----
   const float a1 = __fmul_rn(1.0f - inv_eta, inv_as2);
-  const float b1 = 1.0f - inv_tg;
+  float a2 = __fmul_rn(fmaf(ph, inv_eta, srcQ), inv_as2);
   const float a3 = __fmul_rn(__fmul_rn(C.Dphi3, inv_eta), inv_as2);
+  const float b1 = 1.0f - inv_tg;
+  float b2 = fmaf(U, inv_tg, srcU);
   const float b3 = __fmul_rn(__fmul_rn(3.0f, U), inv_tg);
   if (ST::DEV) {  // deviations: each collision is affine in p_a, slope a1 (b1) times M moves
     a2 = fmaf(a1, ph, a2);  // into the constant term
     b2 = fmaf(b1, U, b2);
   }
-  const float2 K1 = pair(a1, b1);
-  const float2 EA = pair(__fmul_rn(a2, wA), __fmul_rn(b2, wA));
-  const float2 OA = pair(__fmul_rn(a3, -wA), __fmul_rn(b3, wA));
-  const float2 nOA = pair(__fmul_rn(a3, wA), __fmul_rn(b3, -wA));
-  const float2 V1 = pair(Nx, usx), V2 = pair(Ny, usy);  // (c.N, c.u*) of directions 1, 2
-  const float2 V5 = fadd2(V1, V2);                      // direction 5
-  const float2 V6 = pair(Ny - Nx, usy - usx);           // direction 6
-  const float2 q4 = splat(0.25f);
   float c1 = 0.0f, c2 = 0.0f, c3 = 0.0f, c4 = 0.0f;
   if (FLOW) {
     c1 = 1.0f - C.inv_tau_f;
@@ -431,45 +420,20 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   // branch, so the common path stores at fixed shared-memory offsets.
   const auto form = [&](auto mirrored) {
     constexpr bool M = decltype(mirrored)::value;
-    const auto slot = [&](int a) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
       int am = a;
       if constexpr (M) {
         am = mirx ? mirx_of(a) : a;
         am = miry ? miry_of(am) : am;
       }
-      return am * SN + node;
-    };
-    T.hg[slot(1)] = ffma2(K1, hg[1], ffma2(OA, V1, EA));
-    T.hg[slot(2)] = ffma2(K1, hg[2], ffma2(OA, V2, EA));
-    T.hg[slot(3)] = ffma2(K1, hg[3], ffma2(nOA, V1, EA));
-    T.hg[slot(4)] = ffma2(K1, hg[4], ffma2(nOA, V2, EA));
-    T.hg[slot(5)] = ffma2(K1, hg[5], fmul2(q4, ffma2(OA, V5, EA)));
-    T.hg[slot(6)] = ffma2(K1, hg[6], fmul2(q4, ffma2(OA, V6, EA)));
-    T.hg[slot(7)] = ffma2(K1, hg[7], fmul2(q4, ffma2(nOA, V5, EA)));
-    T.hg[slot(8)] = ffma2(K1, hg[8], fmul2(q4, ffma2(nOA, V6, EA)));
-    T.hg[slot(0)] = ffma2(K1, hg[0], fmul2(splat(4.0f), EA));
-    if (FLOW) {
-      const float2 C1 = splat(c1);
-      const float2 C2 = splat(__fmul_rn(c2, wA));
-      const float2 C3 = splat(__fmul_rn(c3, wA)), nC3 = splat(__fmul_rn(c3, -wA));
-      const float2 C4 = splat(__fmul_rn(c4, wA));
-      const float2 cuA = pair(usx, usy);    // c.u* of directions 1, 2 (3, 4: negated)
-      const float2 cuD = pair(V5.y, V6.y);  // directions 5, 6 (7, 8: negated)
-      const float2 eA = ffma2(C4, fmul2(cuA, cuA), C2);
-      const float2 f12 = ffma2(C1, pair(fv[1], fv[2]), ffma2(C3, cuA, eA));
-      T.f[slot(1)] = f12.x;
-      T.f[slot(2)] = f12.y;
-      const float2 f34 = ffma2(C1, pair(fv[3], fv[4]), ffma2(nC3, cuA, eA));
-      T.f[slot(3)] = f34.x;
-      T.f[slot(4)] = f34.y;
-      const float2 eD = ffma2(C4, fmul2(cuD, cuD), C2);
-      const float2 f56 = ffma2(C1, pair(fv[5], fv[6]), fmul2(q4, ffma2(C3, cuD, eD)));
-      T.f[slot(5)] = f56.x;
-      T.f[slot(6)] = f56.y;
-      const float2 f78 = ffma2(C1, pair(fv[7], fv[8]), fmul2(q4, ffma2(nC3, cuD, eD)));
-      T.f[slot(7)] = f78.x;
-      T.f[slot(8)] = f78.y;
-      T.f[slot(0)] = fmaf(c1, fv[0], __fmul_rn(4.0f, C2.x));
+      const int slot = am * SN + node;
+      T.hg[slot] = pair(fmaf(hg[a].x, a1, __fmul_rn(w_of(a), fmaf(-a3, cdot(a, Nx, Ny), a2))),
+                        fmaf(hg[a].y, b1, __fmul_rn(w_of(a), fmaf(b3, cdot(a, usx, usy), b2))));
+      if (FLOW) {
+        const float cu = cdot(a, usx, usy);
+        T.f[slot] = fmaf(fv[a], c1, __fmul_rn(w_of(a), fmaf(fmaf(c4, cu, c3), cu, c2)));
+      }
     }
   };
   if (mirx || miry) form(std::true_type{}); else form(std::false_type{});
