@@ -38,7 +38,7 @@ ALGO_BYTES_PER_LUP = {("f32", 3): 224, ("f32", 2): 152, ("f16", 3): 116, ("f16",
 # what this design moves: + phi^n read; 16-bit storage adds the FP32 moments U (and rho)
 DESIGN_BYTES_PER_LUP = {("f32", 3): 228, ("f32", 2): 156, ("f16", 3): 124, ("f16", 2): 84,
                         ("bf16", 3): 124, ("bf16", 2): 84}
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "march_kernel_traffic.txt")
 NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal (the measured copy peak is the denominator)
 
 
@@ -553,7 +553,7 @@ def run_ours(args):
                 if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_lup": ALGO_BYTES_PER_LUP[("f32", w.lattices)],
                 "design_bytes_per_lup": DESIGN_BYTES_PER_LUP[("f32", w.lattices)],
-                "kernel": "lbmice::march_kernel<flow,F32,prefetch>"}
+                "kernel": "lbmice::march_kernel<flow,F32,plain>"}
     if rec is not None:
         roofline["traffic_source"] = rec.get("source")
         if traffic is None:
@@ -589,7 +589,7 @@ def run_ours(args):
         batched["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                "frac": ach / peak, "traffic": btraffic,
                                "algorithmic_bytes_per_lup": 224,
-                               "kernel": "lbmice::batch_march_kernel<flow,F32,prefetch>"}
+                               "kernel": "lbmice::batch_march_kernel<flow,F32,plain>"}
         if brec is not None:
             batched["roofline"]["traffic_source"] = brec.get("source")
         batched["ms_per_step"] = batched.pop("ms") / batched["steps"]
