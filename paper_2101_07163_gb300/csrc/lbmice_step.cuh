@@ -208,7 +208,7 @@ __device__ __forceinline__ float2 sum9_2(const float2* v) {
 //     r = rho / tau_f, gamma = 1 - 1/(2 tau_f).
 // The projections c.v are sums and exact negations (cdot), so mirror images of a state stay
 // bit-exact mirror images. (h*_a/a_s^2, g*_a) go to shared memory as one pair.
-template <bool FLOW, class S, bool OWN, int R, class ViewAt>
+template <bool FLOW, class S, bool OWN, int R, class ViewAt, bool GHOSTS = true>
 __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& P, int X, int Y,
                                                int node, const ViewAt& view_at,
                                                const PostTile& T, float* hown,
@@ -217,7 +217,8 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   int mx = X, my = Y, shx = 0, shy = 0;
   bool mirx = false, miry = false;
   int inlet = -1;
-  if (X < 0 || X >= C.nx) {
+  // !GHOSTS: the caller knows (X, Y) is inside the grid
+  if (GHOSTS && (X < 0 || X >= C.nx)) {
     const int face = X < 0 ? 0 : 1;
     const int bc = X < 0 ? C.bc[0] : C.bc[1];
     if (bc == BC_PERIODIC) {
@@ -229,7 +230,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
       if (bc == BC_INLET) inlet = face;
     }
   }
-  if (Y < 0 || Y >= C.ny) {
+  if (GHOSTS && (Y < 0 || Y >= C.ny)) {
     const int face = Y < 0 ? 2 : 3;
     const int bc = Y < 0 ? C.bc[2] : C.bc[3];
     if (bc == BC_PERIODIC) {
@@ -247,7 +248,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
   const long long nd = (long long)my * C.rstride + mx;
   const int SN = T.SN;
 
-  if (inlet >= 0) {
+  if (GHOSTS && inlet >= 0) {
     // Inlet ghost: vapour at the inlet state, flow equilibrium at the adjacent density.
     const float ux = inlet == 0 ? C.uin_x[0] : inlet == 1 ? C.uin_x[1]
                    : inlet == 2 ? C.uin_x[2] : C.uin_x[3];
@@ -436,7 +437,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
       }
     }
   };
-  if (mirx || miry) form(std::true_type{}); else form(std::false_type{});
+  if (GHOSTS && (mirx || miry)) form(std::true_type{}); else form(std::false_type{});
   T.B[node] = 1.0f - inv_as2;
 }
 
@@ -658,7 +659,7 @@ struct RingView {
 // row it collided in the pass before (its pre-collision h kept in shared memory). The pull
 // of row r reads the collided rows r - 1 .. r + 1, all in the ring of kMarchPostRows rows.
 // PREF: thread 0 prefetches the boxes of pass k + kMarchAhead into L2 as pass k starts.
-template <bool FLOW, class S, int MODE>
+template <bool FLOW, class S, int MODE, bool EDGE>
 __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, int X0,
                                             int r_begin, int r_end, float* smem) {
   constexpr bool PREF = MODE == MARCH_PREFETCH;
@@ -670,7 +671,7 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
   if (PREF && threadIdx.x == 0)
     for (int j = 0; j < kMarchAhead && r_begin + kMarchRows * j < r_end; ++j)
       prefetch_issue<FLOW, S>(P, X0, r_begin + kMarchRows * j + 1);
-  const bool xin = X0 >= 2 && X0 + 32 <= C.nx;
+  const bool xin = !EDGE || (X0 >= 2 && X0 + 32 <= C.nx);
   // ring slots, kept incrementally: the collided row of warp w in pass k is ring row
   // (pb + w) mod kMarchPostRows of the collided ring and (qb + w) mod kMarchPhiRows of the phi
   // ring, pb = (8k + 2) mod 10, qb = (8k + 3) mod 11 (ring row 0: row r_begin - 1, resp. - 2)
@@ -693,7 +694,7 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
       const int rl = r0 + 2 + w;
       if ((k >= 0 || w >= kMarchRows - 4) && rl <= r_end + 1 && rl <= C.ny + 1) {
         float* row = sphi + wrapQ(qc + 1) * kMarchPW;
-        const bool yin = rl >= 0 && rl < C.ny;
+        const bool yin = !EDGE || (rl >= 0 && rl < C.ny);
         for (int c = lane; c < kMarchPW; c += 32) {
           const int xg = X0 - 2 + c;
           float v;
@@ -723,7 +724,8 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
         return RingView{sphi, wrapQ(q - 1) * kMarchPW, q * kMarchPW, wrapQ(q + 1) * kMarchPW,
                         lane + 1 + shx};
       };
-      collide_source<FLOW, S, true, 1>(C, P, X, rc, sc * 32 + lane, view_at, post, hown);
+      collide_source<FLOW, S, true, 1, decltype(view_at), EDGE>(C, P, X, rc, sc * 32 + lane,
+                                                                view_at, post, hown);
       if (w == kMarchRows - 1) {
         float* st = stash + (k & 1) * 9 * 32;
 #pragma unroll
@@ -771,11 +773,26 @@ constexpr int kMarchMaxSegRows = 64;
 
 // One CTA per (strip, segment): blockIdx.x the strip, blockIdx.y the segment. Held to 64
 // registers (4 CTAs of 256 threads per SM).
+// A CTA whose phi columns X0 - 2 .. X0 + 31 and rows r0 - 2 .. r1 + 1 all lie inside the grid
+// needs no ghost resolution: it runs the march compiled without it (EDGE = false).
+__device__ __forceinline__ bool march_interior(const Consts& C, int X0, int r0, int r1) {
+  return X0 >= 2 && X0 + 32 <= C.nx && r0 >= 2 && r1 + 2 <= C.ny;
+}
+
+template <bool FLOW, class S, int MODE>
+__device__ __forceinline__ void march_cta(const Consts& C, const StepPtrs& P, int X0, int r0,
+                                          int r1, float* smem) {
+  if (march_interior(C, X0, r0, r1))
+    march_range<FLOW, S, MODE, false>(C, P, X0, r0, r1, smem);
+  else
+    march_range<FLOW, S, MODE, true>(C, P, X0, r0, r1, smem);
+}
+
 template <bool FLOW, class S, int MODE>
 __global__ void __launch_bounds__(kMarchThreads, 4) march_kernel(const Consts C, const StepPtrs P) {
   extern __shared__ __align__(16) float march_smem[];
   const int H = C.seg_rows, r0 = blockIdx.y * H;
-  march_range<FLOW, S, MODE>(C, P, blockIdx.x * kMarchCols, r0, min(C.ny, r0 + H), march_smem);
+  march_cta<FLOW, S, MODE>(C, P, blockIdx.x * kMarchCols, r0, min(C.ny, r0 + H), march_smem);
 }
 
 // ---- many grids in one launch ----------------------------------------------------------
@@ -845,7 +862,7 @@ __global__ void __launch_bounds__(kMarchThreads, 4) batch_march_kernel(const __g
   const int seg = local / d.tiles_x, strip = local - seg * d.tiles_x;
   const int H = d.C.seg_rows, r0 = seg * H;
   if (local < 0 || r0 >= d.C.ny) return;
-  march_range<FLOW, S, MODE>(d.C, d.P, strip * kMarchCols, r0, min(d.C.ny, r0 + H), march_smem);
+  march_cta<FLOW, S, MODE>(d.C, d.P, strip * kMarchCols, r0, min(d.C.ny, r0 + H), march_smem);
 }
 
 }  // namespace lbmice
