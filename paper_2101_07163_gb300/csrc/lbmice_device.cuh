@@ -260,6 +260,21 @@ __device__ __forceinline__ float ldg_plane(const float* __restrict__ p, long lon
 __device__ __forceinline__ void st_plane(float* __restrict__ p, long long i, long long n, float v) {
   if (in_range(i, n, OOB_PLANE)) p[i] = v;
 }
+// Element i of a plane copied into shared memory asynchronously (cp.async through L1): the
+// value is there once the issuing thread has passed cp_async_wait_all() and, for the other
+// threads of the block, a barrier after that. An index out of range stores 0 instead.
+__device__ __forceinline__ void cp_async_plane(float* sdst, const float* __restrict__ p,
+                                               long long i, long long n) {
+  if (in_range(i, n, OOB_PLANE)) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(p + i) : "memory");
+  } else {
+    *sdst = 0.0f;
+  }
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
 
 // The 9 deviations d_a = p_a - w_a M of one node and lattice from its 16-bit vector v; the
 // rest one is d_0 = -sum_{a>0} d_a, since the populations sum to M.

@@ -679,6 +679,36 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
   const auto wrapQ = [](int v) { return v < 0 ? v + kMarchPhiRows : (v >= kMarchPhiRows ? v - kMarchPhiRows : v); };
   int pb = (2 - kMarchRows + 2 * kMarchPostRows) % kMarchPostRows;
   int qb = (3 - kMarchRows + 2 * kMarchPhiRows) % kMarchPhiRows;
+  // The phi rows new to pass kk (row r_begin + 8 kk + 2 + w of warp w; the prologue kk = -1:
+  // the four below the first pass) into phi-ring row qrow. Rows inside the grid are copied
+  // asynchronously, so that they arrive while the pass before pulls; ghosts are resolved and
+  // stored directly.
+  const auto phi_rows = [&](int kk, int qrow) {
+    const int rl = r_begin + kMarchRows * kk + 2 + w;
+    if ((kk >= 0 || w >= kMarchRows - 4) && rl <= r_end + 1 && rl <= C.ny + 1) {
+      float* row = sphi + qrow * kMarchPW;
+      const bool yin = !EDGE || (rl >= 0 && rl < C.ny);
+      for (int c = lane; c < kMarchPW; c += 32) {
+        if (!in_range(row - sphi + c, kMarchPN, OOB_SHARED)) continue;
+        const int xg = X0 - 2 + c;
+        if (xin && yin) {
+          cp_async_plane(row + c, P.phi_n, (long long)rl * C.pitch + xg,
+                         (long long)C.pitch * C.ny);
+        } else {
+          int gx, gy;
+          float v = -1.0f;
+          if (xg > C.nx + 1) {
+            v = 0.0f;  // beyond the grid's halo (ragged last strip): never read
+          } else if (axis_phi(xg, C.nx, C.bc[0], C.bc[1], gx) &&
+                     axis_phi(rl, C.ny, C.bc[2], C.bc[3], gy)) {
+            v = ldg_plane(P.phi_n, (long long)gy * C.pitch + gx, (long long)C.pitch * C.ny);
+          }
+          row[c] = v;
+        }
+      }
+    }
+  };
+  phi_rows(-1, wrapQ(wrapQ(qb + w) + 1));
   for (int k = -1;; ++k) {
     const int r0 = r_begin + kMarchRows * k;
     const int rc = r0 + 1 + w;  // collision row of this warp
@@ -689,31 +719,8 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
     if (PREF && threadIdx.x == 0 && k >= 0 && r0 + kMarchRows * kMarchAhead < r_end)
       prefetch_issue<FLOW, S>(P, X0, r0 + kMarchRows * kMarchAhead + 1);
 
-    // ---- A: the new phi rows of this pass (the prologue: the four below the first) ----
-    {
-      const int rl = r0 + 2 + w;
-      if ((k >= 0 || w >= kMarchRows - 4) && rl <= r_end + 1 && rl <= C.ny + 1) {
-        float* row = sphi + wrapQ(qc + 1) * kMarchPW;
-        const bool yin = !EDGE || (rl >= 0 && rl < C.ny);
-        for (int c = lane; c < kMarchPW; c += 32) {
-          const int xg = X0 - 2 + c;
-          float v;
-          if (xin && yin) {
-            v = ldg_plane(P.phi_n, (long long)rl * C.pitch + xg, (long long)C.pitch * C.ny);
-          } else {
-            int gx, gy;
-            v = -1.0f;
-            if (xg > C.nx + 1) {
-              v = 0.0f;  // beyond the grid's halo (ragged last strip): never read
-            } else if (axis_phi(xg, C.nx, C.bc[0], C.bc[1], gx) &&
-                       axis_phi(rl, C.ny, C.bc[2], C.bc[3], gy)) {
-              v = ldg_plane(P.phi_n, (long long)gy * C.pitch + gx, (long long)C.pitch * C.ny);
-            }
-          }
-          if (in_range(row - sphi + c, kMarchPN, OOB_SHARED)) row[c] = v;
-        }
-      }
-    }
+    // ---- A: the phi rows of this pass, issued during the pass before, are in the ring ----
+    cp_async_wait_all();
     __syncthreads();
 
     // ---- B: collide row rc ----
@@ -733,6 +740,13 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
       }
     }
     __syncthreads();
+    // The next pass's phi rows replace ring rows that no collision of this pass reads any more
+    // (rows r0 - 1 .. r0 + 6); the pull does not read the phi ring. The last pass issues none,
+    // so no copy is in flight when the CTA ends.
+    if (r0 + kMarchRows < r_end) {
+      const int qn = wrapQ(qb + kMarchRows);
+      phi_rows(k + 1, wrapQ(wrapQ(qn + w) + 1));
+    }
 
     // ---- C: pull row rp ----
     if (k >= 0) {
