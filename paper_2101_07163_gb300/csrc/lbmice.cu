@@ -32,7 +32,7 @@ constexpr int kTX = 32, kTY = 8; // destination tile of the step kernel
 constexpr int kGraphSteps = 60;
 constexpr int kStatBlocks = 608; // 4 x 152 SMs
 constexpr int kPhases = 6;       // buffer rotation period: populations 2, phi planes 3
-constexpr int kMapsPerPhase = 5; // tensor maps of one step's inputs (StepPtrs::tm)
+constexpr int kMapsPerPhase = 6; // tensor maps of one step's inputs (StepPtrs::tm)
 
 }  // namespace
 
@@ -205,9 +205,10 @@ bool encode_map(CUtensorMap* m, CUtensorMapDataType t, int rank, const void* bas
 // The maps of every step phase (the boxes of one march pass: 8 rows of a strip), encoded on
 // the host and copied to the device once; the buffers never move.
 int make_tensor_maps(lbmice_t* h) {
-  // FP32 storage runs the plain march: prefetching its bandwidth-bound steps measured 15 B
-  // per node of extra DRAM reads and no gain; the issue-bound 16-bit steps gain 3%
-  if (!dev16(h)) return LBMICE_OK;
+  // Every storage: phi^n in boxes of 8 rows x 40 columns, the march's phi ring blocks (slot
+  // 5). The L2 prefetch boxes (slots 0..4) for 16-bit storage only: FP32 storage runs the
+  // plain march, since prefetching its bandwidth-bound steps measured 15 B per node of
+  // extra DRAM reads and no gain, while the issue-bound 16-bit steps gain 3%.
   std::vector<CUtensorMap> maps(kPhases * kMapsPerPhase);
   std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
   const uint64_t P = h->C.pitch, NY = h->C.ny, Q = h->C.pstride;
@@ -217,29 +218,16 @@ int make_tensor_maps(lbmice_t* h) {
     CUtensorMap* m = &maps[ph * kMapsPerPhase];
     const char* pin = static_cast<const char*>(h->pops[ph & 1]);
     const uint64_t d1[2] = {P, NY}, s1[1] = {P * 4};
-    const uint32_t b1[2] = {36, R};
-    if (!dev16(h)) {
-      const uint64_t dq[3] = {4 * P, NY, 4}, sq[2] = {16 * P, 16 * Q};
-      const uint32_t bq[3] = {128, R, 4};
-      ok = ok && encode_map(&m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, pin, dq, sq, bq);
-      const uint64_t d0[2] = {2 * P, NY}, s0[1] = {8 * P};
-      const uint32_t b0[2] = {68, R};
-      ok = ok && encode_map(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pin + 64 * Q, d0, s0, b0);
-      if (h->p.flow) {
-        const uint64_t df[3] = {4 * P, NY, 2};
-        const uint32_t bf[3] = {128, R, 2};
-        ok = ok && encode_map(&m[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, pin + 72 * Q, df, sq, bf);
-        ok = ok && encode_map(&m[3], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pin + 104 * Q, d1, s1, b1);
-      }
-    } else {
-      const uint32_t L = h->p.flow ? 3 : 2;
-      const uint64_t dv[3] = {8 * P, NY, L}, sv[2] = {16 * P, 18 * Q};
-      const uint32_t bv[3] = {256, R, L};
-      ok = ok && encode_map(&m[0], CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, pin, dv, sv, bv);
-      ok = ok && encode_map(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->Um[ph & 1], d1, s1, b1);
-      if (h->p.flow)
-        ok = ok && encode_map(&m[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->rhom[ph & 1], d1, s1, b1);
-    }
+    const uint32_t b1[2] = {36, R}, b5[2] = {kMarchPW, R};
+    ok = ok && encode_map(&m[5], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->phi[ph % 3], d1, s1, b5);
+    if (!dev16(h)) continue;
+    const uint32_t L = h->p.flow ? 3 : 2;
+    const uint64_t dv[3] = {8 * P, NY, L}, sv[2] = {16 * P, 18 * Q};
+    const uint32_t bv[3] = {256, R, L};
+    ok = ok && encode_map(&m[0], CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, pin, dv, sv, bv);
+    ok = ok && encode_map(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->Um[ph & 1], d1, s1, b1);
+    if (h->p.flow)
+      ok = ok && encode_map(&m[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->rhom[ph & 1], d1, s1, b1);
     ok = ok && encode_map(&m[4], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->phi[(ph + 2) % 3], d1, s1, b1);
   }
   if (!ok) return LBMICE_ECUDA;
@@ -328,7 +316,7 @@ int launch_step_ptrs(const lbmice_t* h, const StepPtrs& P, cudaStream_t st) {
         constexpr int M = decltype(pref)::value ? MARCH_PREFETCH : MARCH_PLAIN;
         march_kernel<F, S, M><<<grid, kMarchThreads, march_smem_bytes<F>(), st>>>(h->C, P);
       };
-      const bool pref = P.tm != nullptr;
+      const bool pref = dev16(h) && P.tm != nullptr;
       if (h->p.flow) {
         if (pref) go(std::true_type{}, std::true_type{}); else go(std::true_type{}, std::false_type{});
       } else {
@@ -398,6 +386,14 @@ int run_stats(lbmice_t* h) {
   LB_TRY(cudaMemcpyAsync(h->stat_host, h->stat_out, kNStat * sizeof(double),
                          cudaMemcpyDeviceToHost, h->stream));
   LB_TRY(cudaStreamSynchronize(h->stream));
+  // a bounded device-side wait (the march's phi-ring loads) that gave up since the last check
+  unsigned int w = 0;
+  LB_TRY(cudaMemcpyFromSymbol(&w, lbmice::wait_word, sizeof(w)));
+  if (w) {
+    const unsigned int z = 0;
+    LB_TRY(cudaMemcpyToSymbol(lbmice::wait_word, &z, sizeof(z)));
+    return LBMICE_ETIMEOUT;
+  }
   return LBMICE_OK;
 }
 

@@ -40,9 +40,10 @@ struct StepPtrs {
   float* __restrict__ U_np1;
   const float* __restrict__ rho_n;
   float* __restrict__ rho_np1;
-  // tensor maps of this step's inputs (in device memory) for the march's L2 prefetch:
-  // FP32 (h,g) quads, (h_0,g_0) pairs, f quads, f_0, phi^{n-1}; 16-bit: the deviation
-  // vectors, U^n, rho^n, (unused), phi^{n-1}. Null: no prefetch.
+  // tensor maps of this step's inputs (in device memory), six per step: 16-bit storage's L2
+  // prefetch boxes (deviation vectors, U^n, rho^n, unused, phi^{n-1}; unset for FP32) and
+  // phi^n in the march's phi-ring blocks (slot 5). Null (buffers without maps): no
+  // prefetch, and the phi ring is filled by cp.async.
   const CUtensorMap* tm;
 };
 
@@ -140,31 +141,23 @@ __device__ __forceinline__ void own_load(const Consts& C, const StepPtrs& P, int
 }
 
 // ---- L2 prefetch of a march pass -----------------------------------------------------------
-// The populations a march pass collides (rows y .. y + 7, columns X0 - 1 .. X0 + 30) are
-// prefetched into L2 by TMA a pass ahead, one box per stored plane group, so that the pass's
-// own loads after the phi barrier hit L2: FP32 (h,g) quads [4][8][32 x 4 floats], (h_0,g_0)
-// pairs [8][34 from column X0 - 2], f quads [2][8][32 x 4], f_0 and phi^{n-1} [8][36 from
-// column xa]; 16-bit deviation vectors [3][8][32 x 8 halves], U, rho and phi^{n-1} [8][36],
-// with xa = (X0 - 1) rounded down to a multiple of 4, so that every box starts on a 16-byte
-// boundary (parts outside the grid are skipped). Tensor map slots (StepPtrs::tm): FP32 quads,
-// pairs, f quads, f_0, phi^{n-1}; 16-bit vectors, U, rho, (unused), phi^{n-1}.
+// With 16-bit storage the populations a march pass collides (rows y .. y + 7, columns
+// X0 - 1 .. X0 + 30) are prefetched into L2 by TMA a pass ahead, one box per stored plane
+// group, so that the pass's own loads hit L2: the deviation vectors [3][8][32 x 8 halves],
+// U, rho and phi^{n-1} [8][36 from column xa], xa = (X0 - 1) rounded down to a multiple of 4,
+// so that every box starts on a 16-byte boundary (parts outside the grid are skipped).
+// Tensor map slots (StepPtrs::tm): vectors, U, rho, (unused), phi^{n-1}; slot 5 is the phi^n
+// map of the phi ring. FP32 steps, bandwidth-bound, run the plain march and prefetch nothing.
 // Thread 0: prefetch into L2 the boxes of the pass whose collided rows start at row y.
 template <bool FLOW, class S>
 __device__ __forceinline__ void prefetch_issue(const StepPtrs& P, int X0, int y) {
-  const int xa = (X0 - 1) & ~3;
-  if constexpr (!Storage<S>::DEV) {
-    tma_prefetch_3d(P.tm + 0, 4 * (X0 - 1), y, 0);
-    tma_prefetch_2d(P.tm + 1, 2 * (X0 - 2), y);
-    if (FLOW) {
-      tma_prefetch_3d(P.tm + 2, 4 * (X0 - 1), y, 0);
-      tma_prefetch_2d(P.tm + 3, xa, y);
-    }
-  } else {
+  if constexpr (Storage<S>::DEV) {
+    const int xa = (X0 - 1) & ~3;
     tma_prefetch_3d(P.tm + 0, 8 * (X0 - 1), y, 0);
     tma_prefetch_2d(P.tm + 1, xa, y);
     if (FLOW) tma_prefetch_2d(P.tm + 2, xa, y);
+    tma_prefetch_2d(P.tm + 4, xa, y);
   }
-  tma_prefetch_2d(P.tm + 4, xa, y);
 }
 
 // Deviations (d^h_a, d^g_a) of a node from its two 16-bit vectors; the rest pair is minus the
@@ -618,8 +611,8 @@ constexpr int kMarchRows = 8;                    // rows per pass = warps per CT
 constexpr int kMarchThreads = 32 * kMarchRows;
 constexpr int kMarchCols = 30;                   // destination columns per strip
 constexpr int kMarchPostRows = kMarchRows + 2;   // ring of collided rows
-constexpr int kMarchPhiRows = kMarchRows + 3;    // ring of phi rows
-constexpr int kMarchPW = 34;                     // phi ring row: columns X0 - 2 .. X0 + 31
+constexpr int kMarchPhiRows = 2 * kMarchRows;    // ring of phi rows: two blocks of a pass each
+constexpr int kMarchPW = 40;                     // phi ring row: columns xa .. xa + 39
 constexpr int kMarchSN = kMarchPostRows * 32;
 constexpr int kMarchPN = kMarchPhiRows * kMarchPW;
 
@@ -629,12 +622,16 @@ constexpr int kMarchPN = kMarchPhiRows * kMarchPW;
 enum : int { MARCH_PLAIN = 0, MARCH_PREFETCH = 1 };
 constexpr int kMarchAhead = 1;
 
-// Shared memory of a march CTA: the collided ring, the phi ring and the pre-collision h of
-// warp kMarchRows - 1 for two passes.
+// Shared memory of a march CTA: the collided ring, the phi ring (at a 128-byte boundary:
+// TMA destination), the pre-collision h of warp kMarchRows - 1 for two passes, and the
+// mbarrier of the phi ring's TMA loads.
 template <bool FLOW>
 __host__ __device__ constexpr size_t march_smem_bytes() {
-  return sizeof(float) * (PostTile::floats<FLOW>(kMarchSN) + kMarchPN + 2 * 9 * 32);
+  return sizeof(float) * (PostTile::floats<FLOW>(kMarchSN) + kMarchPN + 2 * 9 * 32) + 8;
 }
+static_assert(PostTile::floats<true>(kMarchSN) % 32 == 0 && PostTile::floats<false>(kMarchSN) % 32 == 0,
+              "phi ring of the march not at a 128-byte boundary");
+static_assert((kMarchRows * kMarchPW * 4) % 128 == 0, "phi ring block not 128-byte aligned");
 
 __host__ __device__ constexpr int march_strips(int nx) { return (nx + kMarchCols - 1) / kMarchCols; }
 
@@ -658,7 +655,13 @@ struct RingView {
 // row r0 + 1 + w) and pulls rows r0 .. r0 + 7: warps 0..6 their own collided row, warp 7 the
 // row it collided in the pass before (its pre-collision h kept in shared memory). The pull
 // of row r reads the collided rows r - 1 .. r + 1, all in the ring of kMarchPostRows rows.
-// PREF: thread 0 prefetches the boxes of pass k + kMarchAhead into L2 as pass k starts.
+// phi^n comes in blocks of 8 rows: block k (rows r0 + 2 .. r0 + 9) is loaded while pass k - 1
+// pulls, into half (k + 1) & 1 of a 16-row ring (grid row r at ring row (r - r_begin + 6) & 15,
+// grid column xa + c at ring column c, xa = (X0 - 2) rounded down to a multiple of 4), so a
+// pass's collisions find rows r0 .. r0 + 9 there. A CTA away from the grid faces whose step
+// has tensor maps loads each block as one TMA box, issued by thread 0 and completing on an
+// mbarrier; the others copy their rows with cp.async (ghost rows and columns resolved).
+// PREF: thread 0 prefetches the populations of pass k + kMarchAhead into L2 as pass k starts.
 template <bool FLOW, class S, int MODE, bool EDGE>
 __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, int X0,
                                             int r_begin, int r_end, float* smem) {
@@ -666,29 +669,42 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
   const PostTile post = PostTile::at<FLOW>(smem, kMarchSN);
   float* sphi = smem + PostTile::floats<FLOW>(kMarchSN);
   float* stash = sphi + kMarchPN;  // [2][9][32]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stash + 2 * 9 * 32);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int X = X0 - 1 + lane;
+  const int xa = (X0 - 2) & ~3;  // grid column of ring column 0 (16-byte aligned)
+  const int po = X0 - 2 - xa;    // ring column of grid column X0 - 2
+  const bool tphi = !EDGE && P.tm != nullptr;
+  if (tphi) {
+    if (threadIdx.x == 0) mbar_init(bar);
+    __syncthreads();
+  }
   if (PREF && threadIdx.x == 0)
     for (int j = 0; j < kMarchAhead && r_begin + kMarchRows * j < r_end; ++j)
       prefetch_issue<FLOW, S>(P, X0, r_begin + kMarchRows * j + 1);
   const bool xin = !EDGE || (X0 >= 2 && X0 + 32 <= C.nx);
-  // ring slots, kept incrementally: the collided row of warp w in pass k is ring row
-  // (pb + w) mod kMarchPostRows of the collided ring and (qb + w) mod kMarchPhiRows of the phi
-  // ring, pb = (8k + 2) mod 10, qb = (8k + 3) mod 11 (ring row 0: row r_begin - 1, resp. - 2)
+  // collided ring: the row of warp w in pass k is ring row (pb + w) mod kMarchPostRows,
+  // pb = (8k + 2) mod 10 (ring row 0: row r_begin - 1), kept incrementally
   const auto wrapP = [](int v) { return v < 0 ? v + kMarchPostRows : (v >= kMarchPostRows ? v - kMarchPostRows : v); };
-  const auto wrapQ = [](int v) { return v < 0 ? v + kMarchPhiRows : (v >= kMarchPhiRows ? v - kMarchPhiRows : v); };
   int pb = (2 - kMarchRows + 2 * kMarchPostRows) % kMarchPostRows;
-  int qb = (3 - kMarchRows + 2 * kMarchPhiRows) % kMarchPhiRows;
-  // The phi rows new to pass kk (row r_begin + 8 kk + 2 + w of warp w; the prologue kk = -1:
-  // the four below the first pass) into phi-ring row qrow. Rows inside the grid are copied
-  // asynchronously, so that they arrive while the pass before pulls; ghosts are resolved and
-  // stored directly.
-  const auto phi_rows = [&](int kk, int qrow) {
-    const int rl = r_begin + kMarchRows * kk + 2 + w;
+  const auto phi_slot = [&](int r) { return (r - r_begin + 6) & (kMarchPhiRows - 1); };
+  // phi^n block kk (rows r_begin + 8 kk + 2 .. + 9; the prologue kk = -1 needs only the last
+  // four) into ring half (kk + 1) & 1
+  const auto phi_block = [&](int kk) {
+    float* half = sphi + ((kk + 1) & 1) * kMarchRows * kMarchPW;
+    const int y0 = r_begin + kMarchRows * kk + 2;
+    if (tphi) {
+      if (threadIdx.x == 0) {
+        mbar_expect(bar, kMarchRows * kMarchPW * sizeof(float));
+        tma_load_2d(half, P.tm + 5, xa, y0, bar);
+      }
+      return;
+    }
+    const int rl = y0 + w;
     if ((kk >= 0 || w >= kMarchRows - 4) && rl <= r_end + 1 && rl <= C.ny + 1) {
-      float* row = sphi + qrow * kMarchPW;
+      float* row = half + w * kMarchPW + po;
       const bool yin = !EDGE || (rl >= 0 && rl < C.ny);
-      for (int c = lane; c < kMarchPW; c += 32) {
+      for (int c = lane; c < 34; c += 32) {
         if (!in_range(row - sphi + c, kMarchPN, OOB_SHARED)) continue;
         const int xg = X0 - 2 + c;
         if (xin && yin) {
@@ -708,28 +724,30 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
       }
     }
   };
-  phi_rows(-1, wrapQ(wrapQ(qb + w) + 1));
+  phi_block(-1);
   for (int k = -1;; ++k) {
     const int r0 = r_begin + kMarchRows * k;
     const int rc = r0 + 1 + w;  // collision row of this warp
     const bool collide = (k >= 0 || w >= kMarchRows - 2) && rc <= r_end && rc <= C.ny &&
                          X <= C.nx;
     const int sc = wrapP(pb + w);  // collided-ring row of rc
-    const int qc = wrapQ(qb + w);  // phi-ring row of rc
     if (PREF && threadIdx.x == 0 && k >= 0 && r0 + kMarchRows * kMarchAhead < r_end)
       prefetch_issue<FLOW, S>(P, X0, r0 + kMarchRows * kMarchAhead + 1);
 
-    // ---- A: the phi rows of this pass, issued during the pass before, are in the ring ----
-    cp_async_wait_all();
+    // ---- A: phi block k, loaded during the pass before, is in the ring ----
+    if (tphi)
+      mbar_wait(bar, (k + 1) & 1);
+    else
+      cp_async_wait_all();
     __syncthreads();
 
     // ---- B: collide row rc ----
     float hown[9];
     if (collide) {
       const auto view_at = [&](int shx, int shy) {
-        const int q = wrapQ(qc + shy);  // phi ring row of the mapped row
-        return RingView{sphi, wrapQ(q - 1) * kMarchPW, q * kMarchPW, wrapQ(q + 1) * kMarchPW,
-                        lane + 1 + shx};
+        const int q = phi_slot(rc + shy);  // phi ring row of the mapped row
+        return RingView{sphi, ((q - 1) & (kMarchPhiRows - 1)) * kMarchPW, q * kMarchPW,
+                        ((q + 1) & (kMarchPhiRows - 1)) * kMarchPW, lane + 1 + shx + po};
       };
       collide_source<FLOW, S, true, 1, decltype(view_at), EDGE>(C, P, X, rc, sc * 32 + lane,
                                                                 view_at, post, hown);
@@ -740,13 +758,10 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
       }
     }
     __syncthreads();
-    // The next pass's phi rows replace ring rows that no collision of this pass reads any more
-    // (rows r0 - 1 .. r0 + 6); the pull does not read the phi ring. The last pass issues none,
-    // so no copy is in flight when the CTA ends.
-    if (r0 + kMarchRows < r_end) {
-      const int qn = wrapQ(qb + kMarchRows);
-      phi_rows(k + 1, wrapQ(wrapQ(qn + w) + 1));
-    }
+    // Block k + 1 replaces the ring half of block k - 1 (rows r0 - 6 .. r0 + 1), which no
+    // collision reads any more; the pull does not read the phi ring. The last pass loads
+    // none, so no copy is in flight when the CTA ends.
+    if (r0 + kMarchRows < r_end) phi_block(k + 1);
 
     // ---- C: pull row rp ----
     if (k >= 0) {
@@ -773,7 +788,6 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
       }
     }
     pb = wrapP(pb + kMarchRows);
-    qb = wrapQ(qb + kMarchRows);
     if (r0 + kMarchRows >= r_end) break;  // rows r_begin .. r0 + 7 are done
   }
 }
@@ -804,7 +818,7 @@ __device__ __forceinline__ void march_cta(const Consts& C, const StepPtrs& P, in
 
 template <bool FLOW, class S, int MODE>
 __global__ void __launch_bounds__(kMarchThreads, 4) march_kernel(const Consts C, const StepPtrs P) {
-  extern __shared__ __align__(16) float march_smem[];
+  extern __shared__ __align__(128) float march_smem[];
   const int H = C.seg_rows, r0 = blockIdx.y * H;
   march_cta<FLOW, S, MODE>(C, P, blockIdx.x * kMarchCols, r0, min(C.ny, r0 + H), march_smem);
 }
@@ -868,7 +882,7 @@ __global__ void __launch_bounds__(TX* TY, 4) batch_step_kernel(const __grid_cons
 // strip-fastest within a member; the members' populations are prefetched as in march_kernel.
 template <bool FLOW, class S, int MODE>
 __global__ void __launch_bounds__(kMarchThreads, 4) batch_march_kernel(const __grid_constant__ BatchLaunch L) {
-  extern __shared__ __align__(16) float march_smem[];
+  extern __shared__ __align__(128) float march_smem[];
   const long long t = blockIdx.x;
   const int m = batch_member_of(L, t);
   const BatchDesc& d = L.d[m];
