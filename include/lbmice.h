@@ -257,8 +257,9 @@ typedef struct lbmice_batch lbmice_batch_t;
 #define LBMICE_SHAPE_32x8 1
 #define LBMICE_SHAPE_64x4 2
 #define LBMICE_SHAPE_16x16 3
-/* Members one batched launch can carry (its parameter block stays under 32 KB). */
-#define LBMICE_BATCH_MAX_PER_LAUNCH 128
+/* Members one batched launch can carry (its parameter block, one 352-byte descriptor per
+ * member, stays under the 32 KB kernel-parameter limit). */
+#define LBMICE_BATCH_MAX_PER_LAUNCH 64
 
 /* Create count member grids from params[0..count-1] on stream (as lbmice_create each), all
  * with the march shape. The batched step is the default scheme only: every member takes the

@@ -340,20 +340,11 @@ int launch_step_ptrs(const lbmice_t* h, const StepPtrs& P, cudaStream_t st) {
   });
 }
 
-// Step s of grid h on its own rotating buffers.
+StepPtrs step_ptrs(const lbmice_t* h, int ph);
+
+// Step s of grid h on its own rotating buffers (phase s mod 6 of the buffer rotation).
 int launch_step(lbmice_t* h, int64_t s, cudaStream_t st) {
-  StepPtrs P;
-  P.pin = h->pops[s & 1];
-  P.pout = h->pops[(s + 1) & 1];
-  P.phi_n = h->phi[s % 3];
-  P.phi_nm1 = h->phi[(s + 2) % 3];
-  P.phi_np1 = h->phi[(s + 1) % 3];
-  P.U_n = h->Um[s & 1];
-  P.U_np1 = h->Um[(s + 1) & 1];
-  P.rho_n = h->rhom[s & 1];
-  P.rho_np1 = h->rhom[(s + 1) & 1];
-  P.tm = h->tmaps ? h->tmaps + kMapsPerPhase * (s % kPhases) : nullptr;
-  return launch_step_ptrs(h, P, st);
+  return launch_step_ptrs(h, step_ptrs(h, (int)(s % kPhases)), st);
 }
 
 int ensure_graph(lbmice_t* h) {
@@ -934,6 +925,19 @@ long long member_units(const lbmice_t* m, int shape) {
 }
 
 // Buffer roles of step phase ph (step mod 6), as the single-grid path rotates them.
+// The region bases of a step's population buffers (StepPtrs::rin, rout): element offsets
+// 4pQ (p = 0..3), 16Q, 18Q, 22Q, 26Q of an FP32 buffer, 9LQ (L = 0, 1, 2) of a 16-bit one.
+void step_regions(StepPtrs& P, const Consts& C, bool dev16) {
+  const long long Q = C.pstride;
+  const long long f32_off[kRegions] = {0, 4 * Q, 8 * Q, 12 * Q, 16 * Q, 18 * Q, 22 * Q, 26 * Q};
+  for (int r = 0; r < kRegions; ++r) {
+    const long long bytes = dev16 ? (r < 3 ? 2 * 9 * r * Q : 0) : 4 * f32_off[r];
+    const bool used = dev16 ? r < 3 : true;
+    P.rin[r] = used ? static_cast<const char*>(P.pin) + bytes : nullptr;
+    P.rout[r] = used ? static_cast<char*>(P.pout) + bytes : nullptr;
+  }
+}
+
 StepPtrs step_ptrs(const lbmice_t* h, int ph) {
   StepPtrs P;
   P.pin = h->pops[ph & 1];
@@ -946,6 +950,7 @@ StepPtrs step_ptrs(const lbmice_t* h, int ph) {
   P.rho_n = h->rhom[ph & 1];
   P.rho_np1 = h->rhom[(ph + 1) & 1];
   P.tm = h->tmaps ? h->tmaps + kMapsPerPhase * ph : nullptr;
+  step_regions(P, h->C, dev16(h));
   return P;
 }
 
@@ -1318,6 +1323,7 @@ StepPtrs tape_step_ptrs(const lbmice_tape_t* t, int j) {
   P.phi_n = t->seg_phi[j + 1];
   P.phi_nm1 = t->seg_phi[j];
   P.phi_np1 = t->seg_phi[j + 2];
+  step_regions(P, t->h->C, dev16(t->h));
   return P;
 }
 

@@ -272,6 +272,23 @@ __device__ __forceinline__ void cp_async_plane(float* sdst, const float* __restr
     *sdst = 0.0f;
   }
 }
+// The same at a 32-bit index, for indices the host has bounded below 2^31 (the plane index
+// y * pitch + x of a grid: lbmice_create refuses larger grids).
+__device__ __forceinline__ float ldg_plane(const float* __restrict__ p, int i, long long n) {
+  return in_range(i, n, OOB_PLANE) ? __ldg(p + i) : 0.0f;
+}
+__device__ __forceinline__ void st_plane(float* __restrict__ p, int i, long long n, float v) {
+  if (in_range(i, n, OOB_PLANE)) p[i] = v;
+}
+__device__ __forceinline__ void cp_async_plane(float* sdst, const float* __restrict__ p, int i,
+                                               long long n) {
+  if (in_range(i, n, OOB_PLANE)) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(p + i) : "memory");
+  } else {
+    *sdst = 0.0f;
+  }
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }

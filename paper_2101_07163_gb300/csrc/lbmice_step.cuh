@@ -45,7 +45,75 @@ struct StepPtrs {
   // phi^n in the march's phi-ring blocks (slot 5). Null (buffers without maps): no
   // prefetch, and the phi ring is filled by cp.async.
   const CUtensorMap* tm;
+  // pin and pout as kRegions region bases, precomputed on the host (step_regions), so that
+  // every population access of a step is a 32-bit node index (node < pstride < 2^31) on a
+  // kernel-parameter base. FP32: the (h,g) quads of directions 1-2, 3-4, 5-6, 7-8 (float4),
+  // the (h_0,g_0) pairs (float2), the f quads 1-4 and 5-8 (float4) and f_0 (float); 16-bit:
+  // the h, g and f deviation vectors (uint4).
+  const void* rin[8];
+  void* rout[8];
 };
+constexpr int kRegions = 8;
+
+// ---- population accesses of a step through the region bases --------------------------------
+__device__ __forceinline__ void load_hg_rg(const Consts& C, const StepPtrs& P, int node,
+                                           float2* hg) {
+  if (!in_range(node, C.pstride, OOB_POPS)) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) hg[a] = make_float2(0.0f, 0.0f);
+    return;
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const float4 v = __ldg(static_cast<const float4*>(P.rin[p]) + node);
+    hg[2 * p + 1] = make_float2(v.x, v.y);
+    hg[2 * p + 2] = make_float2(v.z, v.w);
+  }
+  hg[0] = __ldg(static_cast<const float2*>(P.rin[4]) + node);
+}
+__device__ __forceinline__ void store_hg_rg(const Consts& C, const StepPtrs& P, int node,
+                                            const float2* hg) {
+  if (!in_range(node, C.pstride, OOB_POPS)) return;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+    static_cast<float4*>(P.rout[p])[node] =
+        make_float4(hg[2 * p + 1].x, hg[2 * p + 1].y, hg[2 * p + 2].x, hg[2 * p + 2].y);
+  static_cast<float2*>(P.rout[4])[node] = hg[0];
+}
+__device__ __forceinline__ void load_f_rg(const Consts& C, const StepPtrs& P, int node, float* f) {
+  if (!in_range(node, C.pstride, OOB_POPS)) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) f[a] = 0.0f;
+    return;
+  }
+  const float4 p = __ldg(static_cast<const float4*>(P.rin[5]) + node);
+  const float4 q = __ldg(static_cast<const float4*>(P.rin[6]) + node);
+  f[0] = __ldg(static_cast<const float*>(P.rin[7]) + node);
+  f[1] = p.x;
+  f[2] = p.y;
+  f[3] = p.z;
+  f[4] = p.w;
+  f[5] = q.x;
+  f[6] = q.y;
+  f[7] = q.z;
+  f[8] = q.w;
+}
+__device__ __forceinline__ void store_f_rg(const Consts& C, const StepPtrs& P, int node,
+                                           const float* f) {
+  if (!in_range(node, C.pstride, OOB_POPS)) return;
+  static_cast<float4*>(P.rout[5])[node] = make_float4(f[1], f[2], f[3], f[4]);
+  static_cast<float4*>(P.rout[6])[node] = make_float4(f[5], f[6], f[7], f[8]);
+  static_cast<float*>(P.rout[7])[node] = f[0];
+}
+// 16-bit: the deviation vector of lattice L (0 h, 1 g, 2 f) at a node.
+__device__ __forceinline__ uint4 ldg_vec_rg(const Consts& C, const StepPtrs& P, int L, int node) {
+  return in_range(node, C.pstride, OOB_POPS) ? __ldg(static_cast<const uint4*>(P.rin[L]) + node)
+                                             : make_uint4(0u, 0u, 0u, 0u);
+}
+__device__ __forceinline__ void stg_vec_rg(const Consts& C, const StepPtrs& P, int L, int node,
+                                           uint4 v) {
+  if (in_range(node, C.pstride, OOB_POPS)) static_cast<uint4*>(P.rout[L])[node] = v;
+}
 
 // Collided populations of SN source nodes in shared memory: (h*_a / a_s^2, g*_a) pairs,
 // f*_a, and B = 1 - 1/a_s^2 of every source node.
@@ -121,19 +189,18 @@ __device__ __forceinline__ void own_load(const Consts& C, const StepPtrs& P, int
   using ST = Storage<S>;
   in.valid = X >= 0 && Y >= 0 && X < C.nx && Y < C.ny;
   if (!in.valid) return;
-  const long long idx = (long long)Y * C.pitch + X;
-  const long long nd = (long long)Y * C.rstride + X;
-  const typename ST::T* __restrict__ pops = static_cast<const typename ST::T*>(P.pin);
+  const int idx = Y * C.pitch + X;
+  const int nd = Y * (int)C.rstride + X;
   const long long np = (long long)C.pitch * C.ny;
   if constexpr (!ST::DEV) {
-    load_hg_f32(pops, C.pstride, nd, in.hg);
-    if (FLOW) load_lattice_f32(pops + 18 * C.pstride, C.pstride, nd, in.f);
+    load_hg_rg(C, P, nd, in.hg);
+    if (FLOW) load_f_rg(C, P, nd, in.f);
   } else {
-    in.h = ldg_vec(reinterpret_cast<const uint4*>(pops), nd, C.pstride);
-    in.g = ldg_vec(reinterpret_cast<const uint4*>(pops + 9 * C.pstride), nd, C.pstride);
+    in.h = ldg_vec_rg(C, P, 0, nd);
+    in.g = ldg_vec_rg(C, P, 1, nd);
     in.U = ldg_plane(P.U_n, idx, np);
     if (FLOW) {
-      in.f = ldg_vec(reinterpret_cast<const uint4*>(pops + 18 * C.pstride), nd, C.pstride);
+      in.f = ldg_vec_rg(C, P, 2, nd);
       in.rho = ldg_plane(P.rho_n, idx, np);
     }
   }
@@ -236,9 +303,8 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     }
   }
   using ST = Storage<S>;
-  const long long idx = (long long)my * C.pitch + mx;
-  const typename ST::T* __restrict__ pops = static_cast<const typename ST::T*>(P.pin);
-  const long long nd = (long long)my * C.rstride + mx;
+  const int idx = my * C.pitch + mx;  // < 2^31: lbmice_create refuses larger grids
+  const int nd = my * (int)C.rstride + mx;
   const int SN = T.SN;
 
   if (GHOSTS && inlet >= 0) {
@@ -253,7 +319,7 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
         rho = ldg_plane(P.rho_n, idx, (long long)C.pitch * C.ny);
       } else {
         float fv[9];
-        load_lattice_f32(pops + 18 * C.pstride, C.pstride, nd, fv);
+        load_f_rg(C, P, nd, fv);
         rho = sum9(fv);
       }
     }
@@ -296,16 +362,14 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
     php = pre->php;
   } else {
     if constexpr (!ST::DEV) {
-      load_hg_f32(pops, C.pstride, nd, hg);
-      if (FLOW) load_lattice_f32(pops + 18 * C.pstride, C.pstride, nd, fv);
+      load_hg_rg(C, P, nd, hg);
+      if (FLOW) load_f_rg(C, P, nd, fv);
     } else {
-      const uint4* pv = reinterpret_cast<const uint4*>(pops);
       const long long np = (long long)C.pitch * C.ny;
-      deviations_hg<S>(ldg_vec(pv, nd, C.pstride), ldg_vec(pv + (9 * C.pstride) / 8, nd, C.pstride),
-                       hg);
+      deviations_hg<S>(ldg_vec_rg(C, P, 0, nd), ldg_vec_rg(C, P, 1, nd), hg);
       U = ldg_plane(P.U_n, idx, np);
       if (FLOW) {
-        deviations9<S>(ldg_vec(pv + (18 * C.pstride) / 8, nd, C.pstride), fv);
+        deviations9<S>(ldg_vec_rg(C, P, 2, nd), fv);
         rho = ldg_plane(P.rho_n, idx, np);
       }
     }
@@ -442,9 +506,9 @@ __device__ __forceinline__ void pull_store(const Consts& C, const StepPtrs& P, i
                                            const float* hown) {
   using ST = Storage<S>;
   const int SN = T.SN;
-  const long long idx = (long long)Y * C.pitch + X;
+  const int idx = Y * C.pitch + X;
   const long long np = (long long)C.pitch * C.ny;
-  const long long nd = (long long)Y * C.rstride + X;
+  const int nd = Y * (int)C.rstride + X;
   float2 hg[9];
   float fn[9];
 #pragma unroll
@@ -456,9 +520,8 @@ __device__ __forceinline__ void pull_store(const Consts& C, const StepPtrs& P, i
     if (FLOW) fn[a] = T.f[a * SN + s];
   }
   if constexpr (!ST::DEV) {
-    float* __restrict__ po = static_cast<float*>(P.pout);
-    store_hg_f32(po, C.pstride, nd, hg);
-    if (FLOW) store_lattice_f32(po + 18 * C.pstride, C.pstride, nd, fn);
+    store_hg_rg(C, P, nd, hg);
+    if (FLOW) store_f_rg(C, P, nd, fn);
     const float phin = hg[0].x + (((hg[1].x + hg[3].x) + (hg[2].x + hg[4].x)) +
                                   ((hg[5].x + hg[7].x) + (hg[6].x + hg[8].x)));
     st_plane(P.phi_np1, idx, np, phin);
@@ -475,11 +538,8 @@ __device__ __forceinline__ void pull_store(const Consts& C, const StepPtrs& P, i
       dh[a - 1] = d.x;
       dg[a - 1] = d.y;
     }
-    typename ST::T* __restrict__ pout = static_cast<typename ST::T*>(P.pout);
-    if (in_range(nd, C.pstride, OOB_POPS)) {
-      reinterpret_cast<uint4*>(pout)[nd] = ST::pack8(dh);
-      reinterpret_cast<uint4*>(pout + 9 * C.pstride)[nd] = ST::pack8(dg);
-    }
+    stg_vec_rg(C, P, 0, nd, ST::pack8(dh));
+    stg_vec_rg(C, P, 1, nd, ST::pack8(dg));
     if (FLOW) {
       const float rn = sum9(fn);
       st_plane(P.rho_np1, idx, np, rn);
@@ -490,8 +550,7 @@ __device__ __forceinline__ void pull_store(const Consts& C, const StepPtrs& P, i
         df[a - 1] = d.x;
         df[a] = d.y;
       }
-      if (in_range(nd, C.pstride, OOB_POPS))
-        reinterpret_cast<uint4*>(pout + 18 * C.pstride)[nd] = ST::pack8(df);
+      stg_vec_rg(C, P, 2, nd, ST::pack8(df));
     }
   }
 }
@@ -708,8 +767,7 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
         if (!in_range(row - sphi + c, kMarchPN, OOB_SHARED)) continue;
         const int xg = X0 - 2 + c;
         if (xin && yin) {
-          cp_async_plane(row + c, P.phi_n, (long long)rl * C.pitch + xg,
-                         (long long)C.pitch * C.ny);
+          cp_async_plane(row + c, P.phi_n, rl * C.pitch + xg, (long long)C.pitch * C.ny);
         } else {
           int gx, gy;
           float v = -1.0f;

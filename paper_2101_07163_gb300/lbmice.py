@@ -300,7 +300,7 @@ class Lattice:
 
 
 SHAPES = {0: "march", 1: "32x8", 2: "64x4", 3: "16x16"}  # LBMICE_SHAPE_*
-BATCH_MAX_PER_LAUNCH = 128  # members one batched launch carries (LBMICE_BATCH_MAX_PER_LAUNCH)
+BATCH_MAX_PER_LAUNCH = 64  # members one batched launch carries (LBMICE_BATCH_MAX_PER_LAUNCH)
 
 
 class _Member(Lattice):
