@@ -486,6 +486,12 @@ __device__ __forceinline__ void collide_source(const Consts& C, const StepPtrs& 
         am = miry ? miry_of(am) : am;
       }
       const int slot = am * SN + node;
+      if (a == 0) {  // c_0 = 0: the projection terms vanish exactly (fmaf(x, 0, y) = y)
+        T.hg[slot] = pair(fmaf(hg[0].x, a1, __fmul_rn(w_of(0), a2)),
+                          fmaf(hg[0].y, b1, __fmul_rn(w_of(0), b2)));
+        if (FLOW) T.f[slot] = fmaf(fv[0], c1, __fmul_rn(w_of(0), c2));
+        continue;
+      }
       T.hg[slot] = pair(fmaf(hg[a].x, a1, __fmul_rn(w_of(a), fmaf(-a3, cdot(a, Nx, Ny), a2))),
                         fmaf(hg[a].y, b1, __fmul_rn(w_of(a), fmaf(b3, cdot(a, usx, usy), b2))));
       if (FLOW) {
@@ -760,7 +766,7 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
       return;
     }
     const int rl = y0 + w;
-    if ((kk >= 0 || w >= kMarchRows - 4) && rl <= r_end + 1 && rl <= C.ny + 1) {
+    if ((kk >= 0 || w >= kMarchRows - 4) && rl <= r_end + 1 && (!EDGE || rl <= C.ny + 1)) {
       float* row = half + w * kMarchPW + po;
       const bool yin = !EDGE || (rl >= 0 && rl < C.ny);
       for (int c = lane; c < 34; c += 32) {
@@ -786,8 +792,9 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
   for (int k = -1;; ++k) {
     const int r0 = r_begin + kMarchRows * k;
     const int rc = r0 + 1 + w;  // collision row of this warp
-    const bool collide = (k >= 0 || w >= kMarchRows - 2) && rc <= r_end && rc <= C.ny &&
-                         X <= C.nx;
+    // (an interior CTA's rows and columns all lie inside the grid)
+    const bool collide = (k >= 0 || w >= kMarchRows - 2) && rc <= r_end &&
+                         (!EDGE || (rc <= C.ny && X <= C.nx));
     const int sc = wrapP(pb + w);  // collided-ring row of rc
     if (PREF && threadIdx.x == 0 && k >= 0 && r0 + kMarchRows * kMarchAhead < r_end)
       prefetch_issue<FLOW, S>(P, X0, r0 + kMarchRows * kMarchAhead + 1);
@@ -824,7 +831,7 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
     // ---- C: pull row rp ----
     if (k >= 0) {
       const int rp = w < kMarchRows - 1 ? rc : r0;
-      if (rp < r_end && rp < C.ny && lane >= 1 && lane <= kMarchCols && X < C.nx) {
+      if (rp < r_end && lane >= 1 && lane <= kMarchCols && (!EDGE || (rp < C.ny && X < C.nx))) {
         if (w == kMarchRows - 1) {
           const float* st = stash + ((k - 1) & 1) * 9 * 32;
 #pragma unroll
