@@ -55,6 +55,11 @@ struct StepPtrs {
 };
 constexpr int kRegions = 8;
 
+// Prefetch the line holding p into L1 (an address inside a buffer; nothing to wait for).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // ---- population accesses of a step through the region bases --------------------------------
 __device__ __forceinline__ void load_hg_rg(const Consts& C, const StepPtrs& P, int node,
                                            float2* hg) {
@@ -827,6 +832,21 @@ __device__ __forceinline__ void march_range(const Consts& C, const StepPtrs& P, 
     // collision reads any more; the pull does not read the phi ring. The last pass loads
     // none, so no copy is in flight when the CTA ends.
     if (r0 + kMarchRows < r_end) phi_block(k + 1);
+    // FP32 (latency-bound): this thread's node of the next pass is prefetched into L1 while
+    // this pass pulls; the issue-bound 16-bit steps rely on the TMA prefetch into L2 alone
+    if (!Storage<S>::DEV && !EDGE && rc + kMarchRows <= r_end) {
+      const int rn = rc + kMarchRows;
+      const int ndn = rn * (int)C.rstride + X;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) prefetch_l1(static_cast<const float4*>(P.rin[p]) + ndn);
+      prefetch_l1(static_cast<const float2*>(P.rin[4]) + ndn);
+      if (FLOW) {
+        prefetch_l1(static_cast<const float4*>(P.rin[5]) + ndn);
+        prefetch_l1(static_cast<const float4*>(P.rin[6]) + ndn);
+        prefetch_l1(static_cast<const float*>(P.rin[7]) + ndn);
+      }
+      prefetch_l1(P.phi_nm1 + (rn * C.pitch + X));
+    }
 
     // ---- C: pull row rp ----
     if (k >= 0) {
