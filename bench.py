@@ -434,7 +434,7 @@ def run_gradient(args, stream, dist, n=None, steps=None, fd=True):
                         "design_bytes_per_node_reverse_step": REVERSE_DESIGN_BYTES_PER_NODE,
                         "frac_design_bytes": REVERSE_DESIGN_BYTES_PER_NODE * nodes * steps
                                              / (bwd_ms * 1e-3) / 1e9 / peak,
-                        "kernels": "adj_collide_kernel + adj_pull_kernel + march_kernel "
+                        "kernels": "adj_collide_kernel + adj_stencil_kernel + march_kernel "
                                    "(segment recompute)"},
            "gpu_launches_per_reverse_step": 3}
     if fd:

@@ -312,8 +312,11 @@ int lbmice_batch_destroy(lbmice_batch_t* b);
 typedef struct lbmice_tape lbmice_tape_t;
 
 /* Start a tape on grid h (borrowed; it must outlive the tape), keeping a checkpoint every
- * `every` >= 1 steps. Errors: EINVAL (null, every < 1, h not at step 0, storage other than
- * FP32, a face that is not periodic), ENOMEM, ECUDA. */
+ * `every` >= 1 steps. The reverse step adds the pull's own-population term inside the
+ * collision adjoint when the reverse working set (about 464 bytes per node) exceeds the L2,
+ * else in a separate pass; the environment variable LBMICE_ADJ_FUSED=1 or 0, read here,
+ * forces one form (both give the same bits). Errors: EINVAL (null, every < 1, h not at step
+ * 0, storage other than FP32, a face that is not periodic), ENOMEM, ECUDA. */
 int lbmice_tape_create(lbmice_t* h, int32_t every, lbmice_tape_t** out);
 
 /* Advance the grid by nsteps through lbmice_step, keeping checkpoints. Errors: EINVAL (the

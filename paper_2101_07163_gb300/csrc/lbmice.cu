@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -1232,6 +1233,9 @@ struct lbmice_tape {
   std::vector<float*> plane;       // scratch planes, see enum below
   double* partial = nullptr;       // [blocks][kAdjParams]
   int nblocks = 0;
+  // the pull's own-population term inside the collision adjoint (grids whose reverse working
+  // set, about 4 x 116 B per node, exceeds the L2), else in a separate read-modify-write pass
+  bool fused = false;
   // a full segment's recompute and reverse steps as a CUDA graph, one per starting parity of
   // the adjoint ping-pong (every argument is the same for every full segment)
   cudaGraphExec_t seg_graph[2] = {nullptr, nullptr};
@@ -1348,11 +1352,20 @@ int tape_reverse_step(lbmice_tape_t* t, int j, int cur, cudaStream_t st) {
   A.Bn = t->plane[TP_BN];
   A.partial = t->partial;
   const dim3 g = adj_grid(h);
-  if (h->p.flow)
-    adj_collide_kernel<true><<<g, 256, 0, st>>>(h->C, A);
-  else
-    adj_collide_kernel<false><<<g, 256, 0, st>>>(h->C, A);
-  adj_pull_kernel<<<g, 256, 0, st>>>(h->C, A);
+  if (t->fused) {
+    adj_b_kernel<<<g, 256, 0, st>>>(h->C, A);
+    if (h->p.flow)
+      adj_collide_kernel<true, true><<<g, 256, 0, st>>>(h->C, A);
+    else
+      adj_collide_kernel<false, true><<<g, 256, 0, st>>>(h->C, A);
+    adj_stencil_kernel<<<g, 256, 0, st>>>(h->C, A);
+  } else {
+    if (h->p.flow)
+      adj_collide_kernel<true, false><<<g, 256, 0, st>>>(h->C, A);
+    else
+      adj_collide_kernel<false, false><<<g, 256, 0, st>>>(h->C, A);
+    adj_pull_kernel<<<g, 256, 0, st>>>(h->C, A);
+  }
   return cuda_err(cudaGetLastError());
 }
 
@@ -1396,6 +1409,17 @@ int lbmice_tape_create(lbmice_t* h, int32_t every, lbmice_tape_t** out) {
   if (!t) return LBMICE_ENOMEM;
   t->h = h;
   t->every = every;
+  {
+    // the fused reverse pull for grids whose reverse working set exceeds the L2;
+    // LBMICE_ADJ_FUSED=0 or 1 in the environment forces one form (both give the same bits)
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device) != cudaSuccess) l2 = 0;
+    t->fused = 4.0 * 116.0 * (double)h->C.nx * (double)h->C.ny > (double)l2;
+    if (const char* e = std::getenv("LBMICE_ADJ_FUSED")) {
+      if (e[0] == '0' && e[1] == 0) t->fused = false;
+      if (e[0] == '1' && e[1] == 0) t->fused = true;
+    }
+  }
   const int rc = tape_checkpoint(t);
   if (rc != LBMICE_OK) {
     tape_free(t);

@@ -7,15 +7,23 @@
 // Every coupling reads phi from the phi^n plane (the node's phi and the E4 gradient), which
 // equals sum_a h_a^n on every trajectory, so derivatives along trajectories are the same
 // whichever of the two is differentiated. Given the adjoint of S^{n+1} (pb, Phib, Psib), one
-// reverse step produces the adjoint of S^n in two kernels:
+// reverse step produces the adjoint of S^n in two or three kernels:
 //   adj_collide_kernel (per node x): gathers the adjoints of the pulled values from the
 //     downstream nodes x + c_a, recomputes the collision of x and runs it backwards: writes the
-//     collision part of the population adjoints, the node-local part of the phi^n adjoint,
-//     the adjoint of the node's E4 gradient, the adjoint of phi^{n-1}, B = 1 - 1/a_s^2, and
-//     accumulates the parameter adjoints (FP32 within a warp, FP64 across warps, blocks
-//     and steps; one slot per block: deterministic).
-//   adj_pull_kernel (per node y): adds the pull's own-population term
-//     h_a^{n+1}(y) = h_a^n(y) B(y - c_a) + ..., and gathers the transpose of the E4 stencil.
+//     population adjoints, the node-local part of the phi^n adjoint, the adjoint of the
+//     node's E4 gradient and the adjoint of phi^{n-1}; accumulates the parameter adjoints
+//     (FP32 within a warp, FP64 across warps, blocks and steps; one slot per block:
+//     deterministic). The pull's own-population term h_a^{n+1}(y) = h_a^n(y) B(y - c_a) + ...
+//     (B = 1 - 1/a_s^2) is added in one of two ways:
+//   - grids whose reverse working set fits in L2: adj_collide writes B, then adj_pull_kernel
+//     (per node y) adds the term to the h adjoints (read-modify-write, L2-resident) and
+//     gathers the transpose of the E4 stencil;
+//   - larger grids (FUSED): adj_b_kernel writes B first, adj_collide adds the term as it
+//     writes the h adjoints (each written once), and adj_stencil_kernel gathers the
+//     transpose of the E4 stencil.
+//   Both give the same bits.
+//   adj_stencil_kernel (per node y): the phi^n adjoint, node-local part plus the transpose of
+//     the E4 stencil gathered from the gradient adjoints of the neighbours.
 // Non-differentiable points are taken as the branch the forward step takes: below the
 // |grad phi|^2 threshold a_s = 1 and N = 0 do not depend on the gradient or on eps; q(phi)
 // has zero slope where the clamp to [0, 2] is active.
@@ -41,7 +49,7 @@ struct AdjPtrs {
   float* phib_loc;       // scratch: node-local phi^n adjoint plus Psib_in
   float* gbx;            // scratch: adjoint of the node's E4 gradient, x component
   float* gby;            //   and y component
-  float* Bn;             // scratch: B = 1 - 1/a_s^2 of every node
+  float* Bn;             // scratch: B = 1 - 1/a_s^2 of every node (adj_b_kernel)
   double* partial;       // [blocks][kAdjParams] parameter adjoints, accumulated over steps
 };
 
@@ -78,15 +86,51 @@ __device__ __forceinline__ void block_accumulate(const float* v, double* out) {
   }
 }
 
+// B = 1 - 1/a_s^2 at node (x, y) of a periodic grid, from the E4 gradient of phi^n, with
+// the arithmetic of the collision adjoint's recomputation below.
+__device__ __forceinline__ float adj_node_B(const Consts& C, const float* __restrict__ phi,
+                                            int x, int y) {
+  const long long PI = C.pitch;
+  const int xp = wrap_p(x + 1, C.nx), xm = wrap_m(x - 1, C.nx);
+  const int yp = wrap_p(y + 1, C.ny), ym = wrap_m(y - 1, C.ny);
+  auto P = [&](int xx, int yy) { return __ldg(phi + (long long)yy * PI + xx); };
+  const float pE = P(xp, y), pW = P(xm, y), pN = P(x, yp), pS = P(x, ym);
+  const float pNE = P(xp, yp), pNW = P(xm, yp), pSE = P(xp, ym), pSW = P(xm, ym);
+  const float gx = kW1 * (pE - pW) + kW2 * ((pNE - pNW) + (pSE - pSW));
+  const float gy = kW1 * (pN - pS) + kW2 * ((pNE - pSE) + (pNW - pSW));
+  const float s2 = gx * gx + gy * gy;
+  float as = 1.0f;
+  if (s2 > 1e-12f) {
+    const float rinv = rsqrtf(s2);
+    const float nx = gx * rinv, ny = gy * rinv;
+    const float X2 = nx * nx, Y2 = ny * ny;
+    const float cos6 = X2 * X2 * X2 - 15.0f * X2 * X2 * Y2 + 15.0f * X2 * Y2 * Y2 - Y2 * Y2 * Y2;
+    as = 1.0f + C.eps * cos6;
+  }
+  return 1.0f - __fdividef(1.0f, as * as);
+}
+
+// B of every node into the Bn plane, before the collision adjoint reads it at x - c_a.
+__global__ void __launch_bounds__(256) adj_b_kernel(const Consts C, const AdjPtrs A) {
+  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (x >= C.nx || y >= C.ny) return;
+  A.Bn[(long long)y * C.pitch + x] = adj_node_B(C, A.phi_n, x, y);
+}
+
 // Adjoint of the collision of every node (block 32 x 8, one thread per node). Held to 80
-// registers for 3 CTAs per SM: the 68 bytes of spills this costs the flow form are cheaper
+// registers for 3 CTAs per SM: the bytes of spills this costs the flow form are cheaper
 // than the third CTA's latency hiding is worth (measured 128.6 -> 120.2 ms per reverse sweep).
-template <bool FLOW>
+// FUSED: adds the pull's own-population term to the h adjoints (B from adj_b_kernel); else
+// writes B for adj_pull_kernel.
+template <bool FLOW, bool FUSED>
 __global__ void __launch_bounds__(256, 3) adj_collide_kernel(const Consts C, const AdjPtrs A) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   float part[kAdjParams] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (x < C.nx && y < C.ny) {
+    const float* __restrict__ pb_in = A.pb_in;  // the adjoint ping-pong buffers never alias
+    float* __restrict__ pb_out = A.pb_out;
     const long long Q = C.pstride, R = C.rstride, PI = C.pitch;
     const int xp = wrap_p(x + 1, C.nx), xm = wrap_m(x - 1, C.nx);
     const int yp = wrap_p(y + 1, C.ny), ym = wrap_m(y - 1, C.ny);
@@ -170,12 +214,12 @@ __global__ void __launch_bounds__(256, 3) adj_collide_kernel(const Consts C, con
     for (int a = 0; a < 9; ++a) {
       const int xs = step_to(x, cx_of(a), C.nx), ys = step_to(y, cy_of(a), C.ny);
       const long long jp = (long long)ys * R + xs;
-      const float hhat = __ldg(A.pb_in + (PLANE_H + a) * Q + jp) +
+      const float hhat = __ldg(pb_in + (PLANE_H + a) * Q + jp) +
                          __ldg(A.Phib_in + (long long)ys * PI + xs);
       Ab[a] = hhat;
       Bb += hhat * __ldg(A.pops + f32_pop_index(Q, jp, 0, a));
-      Gb[a] = __ldg(A.pb_in + (PLANE_G + a) * Q + jp);
-      Fb[a] = FLOW ? __ldg(A.pb_in + (PLANE_F + a) * Q + jp) : 0.0f;
+      Gb[a] = __ldg(pb_in + (PLANE_G + a) * Q + jp);
+      Fb[a] = FLOW ? __ldg(pb_in + (PLANE_F + a) * Q + jp) : 0.0f;
     }
 
     // ---- phase field: A_a = h*_a inv_as2, B = 1 - inv_as2,
@@ -302,22 +346,25 @@ __global__ void __launch_bounds__(256, 3) adj_collide_kernel(const Consts C, con
       for (int a = 0; a < 9; ++a)
         fb[a] += rhob + (float)cx_of(a) * jxb + (float)cy_of(a) * jyb;
     }
-    // U = sum g
-#pragma unroll
-    for (int a = 0; a < 9; ++a) gb[a] += Ub;
-
-    // ---- outputs ----
+    // ---- outputs (U = sum g); FUSED: h adds the pull's own-population term ----
+    const float Phb_own = FUSED ? __ldg(A.Phib_in + iq) : 0.0f;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      A.pb_out[(PLANE_H + a) * Q + ip] = hb[a];
-      A.pb_out[(PLANE_G + a) * Q + ip] = gb[a];
-      if (FLOW) A.pb_out[(PLANE_F + a) * Q + ip] = fb[a];
+      if (FUSED) {
+        const float hhat = __ldg(pb_in + (PLANE_H + a) * Q + ip) + Phb_own;
+        const int xs = step_to(x, -cx_of(a), C.nx), ys = step_to(y, -cy_of(a), C.ny);
+        pb_out[(PLANE_H + a) * Q + ip] = hb[a] + hhat * __ldg(A.Bn + (long long)ys * PI + xs);
+      } else {
+        pb_out[(PLANE_H + a) * Q + ip] = hb[a];
+      }
+      pb_out[(PLANE_G + a) * Q + ip] = gb[a] + Ub;
+      if (FLOW) pb_out[(PLANE_F + a) * Q + ip] = fb[a];
     }
     A.phib_loc[iq] = phb + __ldg(A.Psib_in + iq);
     A.gbx[iq] = gxb;
     A.gby[iq] = gyb;
     A.Psib_out[iq] = phpb;
-    A.Bn[iq] = 1.0f - inv_as2;
+    if (!FUSED) A.Bn[iq] = 1.0f - inv_as2;
   }
   const int slot = blockIdx.y * gridDim.x + blockIdx.x;
   block_accumulate(part, A.partial + (long long)slot * kAdjParams);
@@ -354,6 +401,16 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const Consts C, const Adj
     const float hhat = __ldg(A.pb_in + (PLANE_H + a) * Q + ip) + Phb;
     A.pb_out[(PLANE_H + a) * Q + ip] += hhat * __ldg(A.Bn + (long long)ys * PI + xs);
   }
+  A.Phib_out[iq] = __ldg(A.phib_loc + iq) + e4_transpose(C, A.gbx, A.gby, x, y);
+}
+
+// The phi^n adjoint (one thread per node y), once every node's gradient adjoint is known:
+//   Phib_out(y) = phib_loc(y) + sum_e w_e (c_e . gb(y - e)).
+__global__ void __launch_bounds__(256) adj_stencil_kernel(const Consts C, const AdjPtrs A) {
+  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (x >= C.nx || y >= C.ny) return;
+  const long long iq = (long long)y * C.pitch + x;
   A.Phib_out[iq] = __ldg(A.phib_loc + iq) + e4_transpose(C, A.gbx, A.gby, x, y);
 }
 

@@ -146,6 +146,25 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         np.testing.assert_array_equal(ia[k], ic[k])
 
 
+@pytest.mark.parametrize("flow", [True, False], ids=["flow", "noflow"])
+def test_fused_and_separate_reverse_pull_give_the_same_bits(flow, monkeypatch):
+    # grids beyond the L2 add the pull's own-population term inside the collision adjoint
+    # (B from its own pass), smaller ones in a read-modify-write pass; forced either way here
+    w, f = case(flow, nx=64, ny=48)
+    wphi, wU, rng = seeds(w, 15)
+    dirs = {k: rng.uniform(-1, 1, (w.ny, w.nx)) for k in f}
+    got = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("LBMICE_ADJ_FUSED", mode)
+        got[mode] = gpu_gradient(w, f, 19, wphi, wU, dirs, every=6)
+    a, ia = got["0"]
+    b, ib = got["1"]
+    for k in ("eps", "D", "lambda", "init"):
+        assert a[k] == b[k], k
+    for k in ia:
+        np.testing.assert_array_equal(ia[k], ib[k])
+
+
 def test_zero_steps_gives_the_seeds_back():
     w, f = case(True)
     wphi, wU, rng = seeds(w, 14)
