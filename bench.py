@@ -362,7 +362,21 @@ def run_batched(args, stream, dist, rank: int = 0, world: int = 1):
 # 27 + 5 planes (360 B); the pull adjoint reads 9 + 9 population planes and 6 planes, writes
 # 9 + 1 (132 B); the recomputed step moves 228 B.
 REVERSE_ALGO_BYTES_PER_NODE = 3 * 116 + 224
-REVERSE_DESIGN_BYTES_PER_NODE = 360 + 132 + 228
+REVERSE_DESIGN_BYTES_PER_NODE = 360 + 132 + 228  # adj_collide, adj_pull (RMW), recompute
+# beyond L2: adj_b (phi in, B out), adj_collide (+ own h adjoints in, B(x - c_a) in, no B
+# out), adj_stencil, recompute
+REVERSE_DESIGN_BYTES_FUSED = 8 + 400 + 16 + 228
+
+
+def reverse_pull_fused(nodes):
+    """The library's choice of reverse-pull form (lbmice_tape_create): fused when the
+    reverse working set, about 4 x 116 B per node, exceeds the L2 (LBMICE_ADJ_FUSED forces)."""
+    import torch
+    env = os.environ.get("LBMICE_ADJ_FUSED")
+    if env in ("0", "1"):
+        return env == "1"
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    return 4 * 116 * nodes > l2
 
 
 def run_gradient(args, stream, dist, n=None, steps=None, fd=True):
@@ -420,6 +434,8 @@ def run_gradient(args, stream, dist, n=None, steps=None, fd=True):
     lat.close()
     nodes = n * n
     peak, _ = measured_peak()
+    fused = reverse_pull_fused(nodes)
+    design = REVERSE_DESIGN_BYTES_FUSED if fused else REVERSE_DESIGN_BYTES_PER_NODE
     ach = REVERSE_ALGO_BYTES_PER_NODE * nodes * steps / (bwd_ms * 1e-3) / 1e9
     state_mb = 4 * 116 * nodes / 1e6  # state and adjoint, read and written, per step
     out = {"workload": "gradient %dx%d periodic f+g+h, %d steps, checkpoints every 100"
@@ -431,12 +447,15 @@ def run_gradient(args, stream, dist, n=None, steps=None, fd=True):
            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                         "frac": ach / peak,
                         "algorithmic_bytes_per_node_reverse_step": REVERSE_ALGO_BYTES_PER_NODE,
-                        "design_bytes_per_node_reverse_step": REVERSE_DESIGN_BYTES_PER_NODE,
-                        "frac_design_bytes": REVERSE_DESIGN_BYTES_PER_NODE * nodes * steps
+                        "design_bytes_per_node_reverse_step": design,
+                        "frac_design_bytes": design * nodes * steps
                                              / (bwd_ms * 1e-3) / 1e9 / peak,
-                        "kernels": "adj_collide_kernel + adj_stencil_kernel + march_kernel "
-                                   "(segment recompute)"},
-           "gpu_launches_per_reverse_step": 3}
+                        "kernels": ("adj_b_kernel + adj_collide_kernel<fused> + "
+                                    "adj_stencil_kernel" if fused else
+                                    "adj_collide_kernel + adj_pull_kernel")
+                                   + " + march_kernel (segment recompute)"},
+           "reverse_pull": "fused (beyond L2)" if fused else "separate pass (L2-resident)",
+           "gpu_launches_per_reverse_step": 4 if fused else 3}
     if fd:
         h = 1e-3
         base = {"U0": 0.3, "eps": 0.04, "D": 2.0}
