@@ -233,6 +233,15 @@ const char* lbmice_last_error(void);
 int lbmice_debug_flags(uint32_t* flags, int32_t clear);
 int lbmice_debug_set_margin(int64_t margin);
 
+/* Self-test of the bounded device-side waits (both builds). The march's phi-ring waits poll
+ * their mbarrier for about a second at most; one that gives up sets a device word that the
+ * next health check (check_every, lbmice_stats) reports as LBMICE_ETIMEOUT. This call runs
+ * one CTA whose wait cannot be satisfied (an mbarrier phase that expects 16 bytes no copy
+ * brings, nothing in flight), waits for the device, reads and clears the word: it returns
+ * LBMICE_ETIMEOUT when the wait gave up and was reported, LBMICE_OK if it was not. The
+ * context stays usable. Errors: ECUDA. */
+int lbmice_debug_wait_selftest(void);
+
 /* ---- many grids in one launch --------------------------------------------------------------
  * A batch advances many independent grids -- different sizes, supersaturations,
  * anisotropies, inflows and faces -- with one kernel launch per time step for every shape

@@ -811,6 +811,19 @@ int lbmice_debug_flags(uint32_t* flags, int32_t clear) {
 #endif
 }
 
+int lbmice_debug_wait_selftest(void) {
+  unsigned int w = 0;
+  const unsigned int z = 0;
+  LB_TRY(cudaDeviceSynchronize());
+  LB_TRY(cudaMemcpyToSymbol(lbmice::wait_word, &z, sizeof(z)));
+  lbmice::wait_selftest_kernel<<<1, 32>>>();
+  LB_TRY(cudaGetLastError());
+  LB_TRY(cudaDeviceSynchronize());
+  LB_TRY(cudaMemcpyFromSymbol(&w, lbmice::wait_word, sizeof(w)));
+  LB_TRY(cudaMemcpyToSymbol(lbmice::wait_word, &z, sizeof(z)));
+  return w ? LBMICE_ETIMEOUT : LBMICE_OK;
+}
+
 int lbmice_debug_set_margin(int64_t margin) {
   if (margin < 0) return LBMICE_EINVAL;
 #ifdef LBMICE_CHECKED

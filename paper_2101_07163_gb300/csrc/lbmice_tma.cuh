@@ -45,25 +45,42 @@ __device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
                "r"(bytes)
                : "memory");
 }
-// Wait for the phase of the given parity to complete, at most kMbarTries polls; a wait that
-// gives up sets wait_word and returns false (the data are then not to be trusted, and the
-// host reports LBMICE_ETIMEOUT at its next check).
-constexpr int kMbarTries = 1 << 22;
+// Wait for the phase of the given parity to complete: polls that suspend the thread until
+// the phase completes (it wakes then) or for at most 1 ms each (the suspend-time hint bounds
+// the system-dependent limit), at most kMbarTries of them (about a second in all). Suspended
+// warps leave their issue slots to the others. A wait that gives up sets wait_word and returns
+// false (the data are then not to be trusted, and the host reports LBMICE_ETIMEOUT at its
+// next check).
+constexpr int kMbarTries = 1024;
+constexpr uint32_t kMbarSuspendNs = 1000000;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_addr(bar);
   for (int i = 0; i < kMbarTries; ++i) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(kMbarSuspendNs)
         : "memory");
     if (done) return true;
   }
   atomicOr(&wait_word, 1u);
   return false;
 }
+
+// A wait that runs out on purpose (lbmice_debug_wait_selftest): an mbarrier phase that
+// expects 16 bytes no copy delivers. Nothing is in flight when the CTA ends.
+__global__ void wait_selftest_kernel() {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    mbar_expect(&bar, 16);
+  }
+  __syncthreads();
+  mbar_wait(&bar, 0);
+}
+
 // One box of a 2D tensor map into shared memory (16-byte aligned destination, x a multiple
 // of 4 floats), its bytes counted against the mbarrier's current phase.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,

@@ -32,7 +32,7 @@ EXPORTS = ("lbmice_params_default", "lbmice_create", "lbmice_init_seed", "lbmice
            "lbmice_batch_set_shape", "lbmice_batch_destroy", "lbmice_last_error",
            "lbmice_tape_create", "lbmice_tape_record", "lbmice_tape_steps",
            "lbmice_tape_backward", "lbmice_tape_destroy", "lbmice_debug_flags",
-           "lbmice_debug_set_margin", "lbmice_tips")
+           "lbmice_debug_set_margin", "lbmice_debug_wait_selftest", "lbmice_tips")
 
 
 class LbmiceError(RuntimeError):
@@ -110,6 +110,7 @@ def lib():
         L.lbmice_tape_destroy.argtypes = [vp]
         L.lbmice_debug_flags.argtypes = [ctypes.POINTER(ctypes.c_uint32), i32]
         L.lbmice_debug_set_margin.argtypes = [i64]
+        L.lbmice_debug_wait_selftest.argtypes = []
         L.lbmice_tips.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32,
                                   dp, dp]
         _lib = L
