@@ -183,7 +183,8 @@ class ClockSampler:
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for rel in ("paper_2101_07163_gb300/csrc/lbmice_step.cuh",
-                "paper_2101_07163_gb300/csrc/lbmice_device.cuh"):
+                "paper_2101_07163_gb300/csrc/lbmice_device.cuh",
+                "paper_2101_07163_gb300/csrc/lbmice_tma.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
