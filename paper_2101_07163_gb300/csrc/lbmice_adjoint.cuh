@@ -49,7 +49,8 @@ struct AdjPtrs {
   float* phib_loc;       // scratch: node-local phi^n adjoint plus Psib_in
   float* gbx;            // scratch: adjoint of the node's E4 gradient, x component
   float* gby;            //   and y component
-  float* Bn;             // scratch: B = 1 - 1/a_s^2 of every node (adj_b_kernel)
+  float* Bn;             // scratch: B = 1 - 1/a_s^2 of every node (adj_b_kernel, or the
+                         // separate form's adj_collide_kernel)
   double* partial;       // [blocks][kAdjParams] parameter adjoints, accumulated over steps
 };
 
