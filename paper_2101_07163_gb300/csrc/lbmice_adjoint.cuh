@@ -91,10 +91,10 @@ __device__ __forceinline__ void block_accumulate(const float* v, double* out) {
 // the arithmetic of the collision adjoint's recomputation below.
 __device__ __forceinline__ float adj_node_B(const Consts& C, const float* __restrict__ phi,
                                             int x, int y) {
-  const long long PI = C.pitch;
+  const int PI = C.pitch;  // every plane index is below 2^31 (lbmice_create)
   const int xp = wrap_p(x + 1, C.nx), xm = wrap_m(x - 1, C.nx);
   const int yp = wrap_p(y + 1, C.ny), ym = wrap_m(y - 1, C.ny);
-  auto P = [&](int xx, int yy) { return __ldg(phi + (long long)yy * PI + xx); };
+  auto P = [&](int xx, int yy) { return __ldg(phi + (yy * PI + xx)); };
   const float pE = P(xp, y), pW = P(xm, y), pN = P(x, yp), pS = P(x, ym);
   const float pNE = P(xp, yp), pNW = P(xm, yp), pSE = P(xp, ym), pSW = P(xm, ym);
   const float gx = kW1 * (pE - pW) + kW2 * ((pNE - pNW) + (pSE - pSW));
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) adj_b_kernel(const Consts C, const AdjPtr
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= C.nx || y >= C.ny) return;
-  A.Bn[(long long)y * C.pitch + x] = adj_node_B(C, A.phi_n, x, y);
+  A.Bn[y * C.pitch + x] = adj_node_B(C, A.phi_n, x, y);
 }
 
 // Adjoint of the collision of every node (block 32 x 8, one thread per node). Held to 80
@@ -132,11 +132,13 @@ __global__ void __launch_bounds__(256, 3) adj_collide_kernel(const Consts C, con
   if (x < C.nx && y < C.ny) {
     const float* __restrict__ pb_in = A.pb_in;  // the adjoint ping-pong buffers never alias
     float* __restrict__ pb_out = A.pb_out;
-    const long long Q = C.pstride, R = C.rstride, PI = C.pitch;
+    // plane strides in 64 bits; node and plane indices below 2^31 (lbmice_create)
+    const long long Q = C.pstride;
+    const int R = (int)C.rstride, PI = C.pitch;
     const int xp = wrap_p(x + 1, C.nx), xm = wrap_m(x - 1, C.nx);
     const int yp = wrap_p(y + 1, C.ny), ym = wrap_m(y - 1, C.ny);
-    const long long ip = (long long)y * R + x;  // population offset of the node
-    const long long iq = (long long)y * PI + x;  // plane offset of the node
+    const int ip = y * R + x;   // population offset of the node
+    const int iq = y * PI + x;  // plane offset of the node
 
     // ---- forward recomputation of the node's collision (the step kernel's quantities, in
     //      their unfactored form; values agree with the kernel's to rounding) ----
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(256, 3) adj_collide_kernel(const Consts C, con
       jx = sumcx9(fv);
       jy = sumcy9(fv);
     }
-    auto P = [&](int xx, int yy) { return __ldg(A.phi_n + (long long)yy * PI + xx); };
+    auto P = [&](int xx, int yy) { return __ldg(A.phi_n + (yy * PI + xx)); };
     const float pE = P(xp, y), pW = P(xm, y), pN = P(x, yp), pS = P(x, ym);
     const float pNE = P(xp, yp), pNW = P(xm, yp), pSE = P(xp, ym), pSW = P(xm, ym);
     const float gx = kW1 * (pE - pW) + kW2 * ((pNE - pNW) + (pSE - pSW));
@@ -214,9 +216,9 @@ __global__ void __launch_bounds__(256, 3) adj_collide_kernel(const Consts C, con
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const int xs = step_to(x, cx_of(a), C.nx), ys = step_to(y, cy_of(a), C.ny);
-      const long long jp = (long long)ys * R + xs;
+      const int jp = ys * R + xs;
       const float hhat = __ldg(pb_in + (PLANE_H + a) * Q + jp) +
-                         __ldg(A.Phib_in + (long long)ys * PI + xs);
+                         __ldg(A.Phib_in + (ys * PI + xs));
       Ab[a] = hhat;
       Bb += hhat * __ldg(A.pops + f32_pop_index(Q, jp, 0, a));
       Gb[a] = __ldg(pb_in + (PLANE_G + a) * Q + jp);
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(256, 3) adj_collide_kernel(const Consts C, con
       if (FUSED) {
         const float hhat = __ldg(pb_in + (PLANE_H + a) * Q + ip) + Phb_own;
         const int xs = step_to(x, -cx_of(a), C.nx), ys = step_to(y, -cy_of(a), C.ny);
-        pb_out[(PLANE_H + a) * Q + ip] = hb[a] + hhat * __ldg(A.Bn + (long long)ys * PI + xs);
+        pb_out[(PLANE_H + a) * Q + ip] = hb[a] + hhat * __ldg(A.Bn + (ys * PI + xs));
       } else {
         pb_out[(PLANE_H + a) * Q + ip] = hb[a];
       }
@@ -375,11 +377,11 @@ __global__ void __launch_bounds__(256, 3) adj_collide_kernel(const Consts C, con
 // at z reads phi(z + e) with weight w_e c_e (e = (1,0) is read by z = (x-1, y), and so on).
 __device__ __forceinline__ float e4_transpose(const Consts& C, const float* __restrict__ gbx,
                                               const float* __restrict__ gby, int x, int y) {
-  const long long PI = C.pitch;
+  const int PI = C.pitch;
   const int xp = wrap_p(x + 1, C.nx), xm = wrap_m(x - 1, C.nx);
   const int yp = wrap_p(y + 1, C.ny), ym = wrap_m(y - 1, C.ny);
-  auto GX = [&](int xx, int yy) { return __ldg(gbx + (long long)yy * PI + xx); };
-  auto GY = [&](int xx, int yy) { return __ldg(gby + (long long)yy * PI + xx); };
+  auto GX = [&](int xx, int yy) { return __ldg(gbx + (yy * PI + xx)); };
+  auto GY = [&](int xx, int yy) { return __ldg(gby + (yy * PI + xx)); };
   const float axis = kW1 * ((GX(xm, y) - GX(xp, y)) + (GY(x, ym) - GY(x, yp)));
   const float diag = kW2 * ((GX(xm, ym) - GX(xp, yp)) + (GX(xm, yp) - GX(xp, ym)) +
                             (GY(xm, ym) - GY(xp, yp)) + (GY(xp, ym) - GY(xm, yp)));
@@ -393,14 +395,15 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const Consts C, const Adj
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= C.nx || y >= C.ny) return;
-  const long long Q = C.pstride, R = C.rstride, PI = C.pitch;
-  const long long ip = (long long)y * R + x, iq = (long long)y * PI + x;
+  const long long Q = C.pstride;
+  const int R = (int)C.rstride, PI = C.pitch;
+  const int ip = y * R + x, iq = y * PI + x;
   const float Phb = __ldg(A.Phib_in + iq);
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const int xs = step_to(x, -cx_of(a), C.nx), ys = step_to(y, -cy_of(a), C.ny);
     const float hhat = __ldg(A.pb_in + (PLANE_H + a) * Q + ip) + Phb;
-    A.pb_out[(PLANE_H + a) * Q + ip] += hhat * __ldg(A.Bn + (long long)ys * PI + xs);
+    A.pb_out[(PLANE_H + a) * Q + ip] += hhat * __ldg(A.Bn + (ys * PI + xs));
   }
   A.Phib_out[iq] = __ldg(A.phib_loc + iq) + e4_transpose(C, A.gbx, A.gby, x, y);
 }
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(256) adj_stencil_kernel(const Consts C, const 
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= C.nx || y >= C.ny) return;
-  const long long iq = (long long)y * C.pitch + x;
+  const int iq = y * C.pitch + x;
   A.Phib_out[iq] = __ldg(A.phib_loc + iq) + e4_transpose(C, A.gbx, A.gby, x, y);
 }
 
